@@ -1,0 +1,182 @@
+/*
+ * hough.h -- C ABI of the GB300 conformal Hough hit filter (libhough.so).
+ *
+ * The library runs the hot path of the matrix-based conformal Hough transform
+ * for drift-chamber hit filtering on an sm_103a GPU:
+ *
+ *   map     conformal map of every hit, Eq. (1) (with the factor 2 that makes
+ *           Eq. (2) hold): u = 2x/r^2, v = 2y/r^2, in fixed point
+ *           u_q = floor(2 x 2^32 / (x^2 + y^2)), x, y in integer micrometres
+ *   rho     the hits x theta-bins matrix R of Sec. 3:
+ *           rho_q(i, j) = u_q(i) c_j + v_q(i) s_j with c_j = round(2^14 cos th_j),
+ *           s_j = round(2^14 sin th_j), th_j = (j + 1/2) pi / N_theta
+ *   vote    k = clamp(floor((rho_q + H) N_rho / (2H)), 0, N_rho - 1), acc[j][k] += 1,
+ *           H = 703687442 = 0.01 mm^-1 in units of 2^-46 um^-1 (the rho range
+ *           [-0.01, 0.01] of Sec. 2); one int16 accumulator [N_theta][N_rho] per event
+ *   peaks   cells with acc >= threshold that are 3x3 local maxima (Sec. 2 peak
+ *           finding with neighbourhood suppression); ties: strictly above the
+ *           neighbours that precede the cell in raster (theta-major) order, at least
+ *           equal to those that follow; theta wraps (column -1 is column N_theta-1 and
+ *           column N_theta is column 0, both with k -> N_rho-1-k); neighbours past the
+ *           rho edges are skipped; peaks listed in raster order
+ *   select  back-projection filter (Sec. 2 "data filtering"): a hit is kept when, at
+ *           the theta column of some stored peak, its rho bin is within
+ *           keep_halfwidth of the peak's rho bin
+ *
+ * All arithmetic is integer, so results are exact and reproducible.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *     pointers. The library allocates no device memory in any entry point.
+ *   - Hits: int32 (x, y) pairs in micrometres, |x|, |y| <= 2^24, stored
+ *     interleaved (8 bytes per hit, 8-byte aligned). Event e owns hits
+ *     [off[e], off[e+1]) of an int64 offsets array with off[0] = 0,
+ *     non-decreasing, off[n_events] = n_hits.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as void*,
+ *     NULL = legacy default stream) and the call returns without synchronising.
+ *   - Return value: HOUGH_OK or a negative HOUGH_E* code for faults the host can
+ *     see (nothing is enqueued then). Faults only the device can see are OR-ed as
+ *     HOUGH_F_* bits into the caller's status buffer d_status (int32[4], zeroed by
+ *     the caller before first use; word 0 holds the sticky flags, words 1..3 are
+ *     per-call scratch). Read it with hough_status(). Calls that run concurrently
+ *     must use distinct status buffers.
+ *   - A hit with r = 0 or a coordinate beyond 2^24 um sets HOUGH_F_BAD_HIT and
+ *     neither votes nor is kept. An event with more than HOUGH_MAX_EVENT_HITS
+ *     hits sets HOUGH_F_EVENT_TOO_LARGE and yields zero accumulator, no peaks and
+ *     no kept hits. Offsets that break the rules above set HOUGH_F_BAD_OFFSETS
+ *     and no output of that call is written.
+ */
+#ifndef HOUGH_H
+#define HOUGH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define HOUGH_OK 0
+#define HOUGH_EINVAL (-1)     /* null pointer or negative count */
+#define HOUGH_EPARAM (-2)     /* hough_params out of range */
+#define HOUGH_ESMEM (-3)      /* requested shape does not fit shared memory */
+#define HOUGH_ECUDA (-4)      /* CUDA runtime error (see hough_last_cuda_error) */
+#define HOUGH_EWORKSPACE (-5) /* workspace too small */
+#define HOUGH_ETIMEDOUT (-6)  /* a bounded wait gave up */
+#define HOUGH_EFULL (-7)      /* serving admission refused: no free slot */
+#define HOUGH_EDEVICE (-8)    /* device-side status flags are set */
+
+/* ---- device status flags (word 0 of d_status) ---- */
+#define HOUGH_F_BAD_HIT 1
+#define HOUGH_F_BAD_OFFSETS 2
+#define HOUGH_F_PEAK_OVERFLOW 4 /* an event had more than max_peaks peaks: the first
+                                   max_peaks in raster order are stored and used */
+#define HOUGH_F_EVENT_TOO_LARGE 8
+#define HOUGH_F_TIMEOUT 16
+
+#define HOUGH_STATUS_WORDS 4
+#define HOUGH_MAX_EVENT_HITS 32767
+#define HOUGH_RHO_HALF_RANGE 703687442LL /* H */
+
+/* Algorithm and launch parameters. Zero in a launch field means "choose". */
+typedef struct hough_params {
+  int32_t n_theta;        /* N_theta in [4, 1024] */
+  int32_t n_rho;          /* N_rho in [4, 1024] */
+  int32_t threshold;      /* absolute vote threshold, >= 1 */
+  int32_t keep_halfwidth; /* rho-bin half-width of the selection window, >= 0 */
+  int32_t max_peaks;      /* stored peaks per event, in [1, 65536] */
+  int32_t theta_tiles;    /* theta tiles per event (0 = auto); each tile is one CTA */
+  int32_t events_per_cta; /* persistent queue: work items taken per pop (0 = auto) */
+  int32_t block;          /* threads per CTA (0 = auto) */
+} hough_params;
+
+/* One peak: theta bin j, rho bin k, votes acc[j][k], flags (reserved, 0). 8 bytes. */
+typedef struct hough_peak {
+  int16_t theta_bin;
+  int16_t rho_bin;
+  int16_t votes;
+  int16_t flags;
+} hough_peak;
+
+/* ---- stepwise entry points (the accumulator goes through HBM; used for parity) ---- */
+
+/* Conformal map, Eq. (1)/(2): d_uq[i], d_vq[i] = u_q, v_q of hit i (int64, n_hits each).
+ * A bad hit gets INT64_MIN in both and sets HOUGH_F_BAD_HIT. d_off is validated only. */
+int hough_map(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, int64_t* d_uq,
+              int64_t* d_vq, int32_t* d_status, void* stream);
+
+/* Voting over the rho matrix (Sec. 3): d_acc = int16 [n_events][n_theta][n_rho], raster
+ * (theta-major) order, fully overwritten. Hits whose d_uq is INT64_MIN are skipped. */
+int hough_vote(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+               const hough_params* p, int16_t* d_acc, int32_t* d_status, void* stream);
+
+/* Peak finding on d_acc (layout as written by hough_vote): d_npeaks[e] = true peak count,
+ * d_peaks = [n_events][max_peaks], the first min(count, max_peaks) in raster order, rest zeroed. */
+int hough_peaks(const int16_t* d_acc, int64_t n_events, const hough_params* p, int32_t* d_npeaks,
+                hough_peak* d_peaks, int32_t* d_status, void* stream);
+
+/* Back-projection selection: d_mask[i] = 1 if hit i is kept, else 0; d_nkept[e] = kept hits of e. */
+int hough_select(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                 const hough_params* p, const int32_t* d_npeaks, const hough_peak* d_peaks, uint8_t* d_mask,
+                 int32_t* d_nkept, int32_t* d_status, void* stream);
+
+/* ---- fused path (the accumulator never leaves shared memory) ---- */
+
+/* Device workspace bytes that hough_run / hough_run_batched need for these parameters
+ * and batch size (0 is never returned). */
+size_t hough_workspace_size(const hough_params* p, int64_t n_events);
+
+/* Whole path in one pass: map -> rho -> vote -> peaks -> select for every event.
+ * Outputs as in the stepwise calls; d_checksum (nullable) gets per event
+ * sum over cells c = j*n_rho + k of acc[c] * splitmix64_finalizer(c + 1) mod 2^64.
+ * d_ws: workspace of ws_bytes >= hough_workspace_size(p, n_events), 256-byte aligned.
+ * One CTA per (event, theta tile). */
+int hough_run(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, const hough_params* p,
+              int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask, int32_t* d_nkept, uint64_t* d_checksum,
+              void* d_ws, size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* Same results as hough_run, scheduled as one persistent launch: CTAs pop
+ * (event, tile) work items, largest events first, from a queue in d_ws. The
+ * validation/ordering kernel and the persistent kernel are replayed as a CUDA
+ * graph cached per (pointers, sizes, parameters, stream). */
+int hough_run_batched(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                      const hough_params* p, int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask,
+                      int32_t* d_nkept, uint64_t* d_checksum, void* d_ws, size_t ws_bytes, int32_t* d_status,
+                      void* stream);
+
+/* Launch shape the library would use for these parameters: fills the zero launch fields
+ * of *p (theta_tiles, events_per_cta, block) and returns HOUGH_OK or an error. */
+int hough_resolve_params(hough_params* p);
+
+/* Synchronises `stream`, copies word 0 of d_status into *host_flags and returns
+ * HOUGH_OK if it is 0, else HOUGH_EDEVICE. */
+int hough_status(const int32_t* d_status, void* stream, int32_t* host_flags);
+
+/* Static description of a return code or of a single HOUGH_F_* flag value. */
+const char* hough_strerror(int code);
+
+/* Last CUDA runtime error code seen by the library on this host thread (0 if none). */
+int hough_last_cuda_error(void);
+
+/* ---- measurement and self-test entry points ---- */
+
+/* Exhaustively checks the device rho-bin function against plain 64-bit integer
+ * division over rho in [rho_lo, rho_hi]: *d_mismatch (uint64, caller-zeroed) gets
+ * the number of disagreements. */
+int hough_selftest_bin(int32_t n_rho, int64_t rho_lo, int64_t rho_hi, unsigned long long* d_mismatch,
+                       void* stream);
+
+/* Shared-memory atomic ceiling: every SM runs `ctas_per_sm` CTAs of `threads` threads,
+ * each thread issuing `iters` x 16 32-bit shared-memory adds into a `smem_bytes`
+ * array with address pattern `mode` (0: each lane its own bank, conflict-free;
+ * 1: pseudo-random words; 2: all lanes of a warp on one word). *d_sink receives a
+ * value that keeps the work alive. Time it with events on `stream`. */
+int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,
+                             unsigned long long* d_sink, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOUGH_H */
