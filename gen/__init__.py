@@ -85,17 +85,19 @@ class EventConfig:
 
 # The five workloads: plain small, plain paper-scale, batched, served (same event
 # distribution as batched), high-occupancy stress. Seeds are 0x5EED0000 + index.
+# max_peaks is sized above the largest peak count seen in each workload, so no
+# event overflows its peak list.
 CONFIGS = {
     "plain_small": EventConfig("plain_small", 100, 0x5EED0000, 0, 2, 2, 0.0, 0, 200.0, 1000.0, 0, 0.05, 0.05,
                                64, 64, 12),
     "plain_paper": EventConfig("plain_paper", 1000, 0x5EED0001, 1, 2, 8, 0.0, 1, 50.0, 1500.0, 0, 0.10, 0.10,
-                               256, 256, 16),
+                               256, 256, 16, max_peaks=2048),
     "batched": EventConfig("batched", 100000, 0x5EED0002, 2, 0, 16, 4.0, 1, 50.0, 1500.0, 1, 0.05, 0.30,
-                           256, 256, 16),
+                           256, 256, 16, max_peaks=4096),
     "served": EventConfig("served", 100000, 0x5EED0003, 2, 0, 16, 4.0, 1, 50.0, 1500.0, 1, 0.05, 0.30,
-                          256, 256, 16),
+                          256, 256, 16, max_peaks=4096),
     "stress": EventConfig("stress", 10000, 0x5EED0004, 0, 16, 16, 0.0, 2, 120.0, 1500.0, 0, 0.40, 0.40,
-                          512, 512, 20, pt_frac=0.4, pt_a2=50.0, pt_b2=120.0),
+                          512, 512, 20, pt_frac=0.4, pt_a2=50.0, pt_b2=120.0, max_peaks=16384),
 }
 
 

@@ -112,7 +112,8 @@ int hough_vote(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const i
                const hough_params* p, int16_t* d_acc, int32_t* d_status, void* stream);
 
 /* Peak finding on d_acc (layout as written by hough_vote): d_npeaks[e] = true peak count,
- * d_peaks = [n_events][max_peaks], the first min(count, max_peaks) in raster order, rest zeroed. */
+ * d_peaks = [n_events][max_peaks], the first min(count, max_peaks) in raster order; entries past
+ * them are left unchanged (this holds for every entry point that writes peaks). */
 int hough_peaks(const int16_t* d_acc, int64_t n_events, const hough_params* p, int32_t* d_npeaks,
                 hough_peak* d_peaks, int32_t* d_status, void* stream);
 
@@ -144,6 +145,27 @@ int hough_run_batched(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off,
                       const hough_params* p, int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask,
                       int32_t* d_nkept, uint64_t* d_checksum, void* d_ws, size_t ws_bytes, int32_t* d_status,
                       void* stream);
+
+/* End-to-end form for callers holding HOST buffers (pinned memory recommended): copies
+ * h_xy/h_off to the device, runs the batched path, packs the stored peaks densely and
+ * copies the results back, then synchronises `stream`. Outputs: h_npeaks[n_events] (true
+ * counts), h_peak_off[n_events + 1] (offsets of each event's stored peaks in h_peaks),
+ * h_peaks[<= h_peaks_cap], h_mask[n_hits], h_nkept[n_events]. d_buf is a device staging
+ * buffer of d_buf_bytes >= hough_host_buffer_size(p, n_hits, n_events) bytes, 256-byte
+ * aligned. Returns HOUGH_EWORKSPACE if the stored peaks exceed h_peaks_cap (h_peak_off is
+ * valid then), or HOUGH_EDEVICE if device flags were raised (outputs are valid). */
+int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, int64_t n_events, const hough_params* p,
+                   int32_t* h_npeaks, int64_t* h_peak_off, hough_peak* h_peaks, int64_t h_peaks_cap, uint8_t* h_mask,
+                   int32_t* h_nkept, void* d_buf, size_t d_buf_bytes, int32_t* d_status, void* stream);
+
+/* Device staging bytes hough_run_host needs. */
+size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_events);
+
+/* Measurement hook for the calling host thread: when both are non-NULL, later fused and
+ * batched calls record the CUDA events begin/end (cudaEvent_t passed as void*) on their
+ * stream immediately before and after the main fused kernel, so its duration can be read
+ * with cudaEventElapsedTime. NULL, NULL turns it off. Graph replays are cached per pair. */
+void hough_set_stage_events(void* begin, void* end);
 
 /* Launch shape the library would use for these parameters: fills the zero launch fields
  * of *p (theta_tiles, events_per_cta, block) and returns HOUGH_OK or an error. */

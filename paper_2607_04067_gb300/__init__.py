@@ -1,0 +1,307 @@
+"""GB300 conformal Hough hit filter: thin Python binding over ``libhough.so``.
+
+Every step runs in the library's sm_103a kernels; this module only marshals
+torch CUDA tensors (device memory, streams) into the C ABI of
+``include/hough.h``. There is no CPU fallback: if the library cannot be built
+or loaded, or a tensor is not on a CUDA device, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from dataclasses import dataclass
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, EPARAM, ESMEM, ECUDA, EWORKSPACE, ETIMEDOUT, EFULL, EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+F_BAD_HIT, F_BAD_OFFSETS, F_PEAK_OVERFLOW, F_EVENT_TOO_LARGE, F_TIMEOUT = 1, 2, 4, 8, 16
+STATUS_WORDS = 4
+MAX_EVENT_HITS = 32767
+HEADER = os.path.join(_build.ROOT, "include", "hough.h")
+
+
+class HoughError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        lib = load()
+        msg = lib.hough_strerror(code).decode()
+        if code == ECUDA:
+            msg += f" (cudaError {lib.hough_last_cuda_error()})"
+        super().__init__(f"{fn}: {msg} [{code}]")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "n_theta", "n_rho", "threshold", "keep_halfwidth", "max_peaks", "theta_tiles", "events_per_cta", "block")]
+
+    def __repr__(self):
+        return "Params(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
+
+
+def params(n_theta: int, n_rho: int, threshold: int, keep_halfwidth: int = 1, max_peaks: int = 1024,
+           theta_tiles: int = 0, events_per_cta: int = 0, block: int = 0) -> Params:
+    return Params(n_theta, n_rho, threshold, keep_halfwidth, max_peaks, theta_tiles, events_per_cta, block)
+
+
+def declared_symbols() -> list[str]:
+    """Names of the entry points declared in include/hough.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(hough_\w+)\s*\(", text, flags=re.M)))
+
+
+def load(build: bool = True):
+    """Loads (building first if sources changed) libhough.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            lib = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            P = ctypes.POINTER(Params)
+            sig = {
+                "hough_map": [vp, i64, vp, i64, vp, vp, vp, vp],
+                "hough_vote": [vp, vp, i64, vp, i64, P, vp, vp, vp],
+                "hough_peaks": [vp, i64, P, vp, vp, vp, vp],
+                "hough_select": [vp, vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp],
+                "hough_run": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp],
+                "hough_run_batched": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp],
+                "hough_resolve_params": [P],
+                "hough_status": [vp, vp, ctypes.POINTER(i32)],
+                "hough_last_cuda_error": [],
+                "hough_selftest_bin": [i32, i64, i64, vp, vp],
+                "hough_probe_smem_atomics": [i32, i32, i32, i32, i32, vp, vp],
+                "hough_run_host": [vp, i64, vp, i64, P, vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp, vp],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.hough_workspace_size.argtypes = [P, i64]
+            lib.hough_workspace_size.restype = ctypes.c_size_t
+            lib.hough_host_buffer_size.argtypes = [P, i64, i64]
+            lib.hough_host_buffer_size.restype = ctypes.c_size_t
+            lib.hough_set_stage_events.argtypes = [vp, vp]
+            lib.hough_set_stage_events.restype = None
+            lib.hough_strerror.argtypes = [ctypes.c_int]
+            lib.hough_strerror.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+# ---------------------------------------------------------------- torch marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(t, name, dtype=None):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(fn, rc):
+    if rc != OK:
+        raise HoughError(fn, rc)
+
+
+def new_status(device="cuda"):
+    torch = _torch()
+    return torch.zeros(STATUS_WORDS, dtype=torch.int32, device=device)
+
+
+def status(st, stream=None) -> int:
+    """Synchronises the stream and returns the sticky device flags (word 0)."""
+    flags = ctypes.c_int32(0)
+    rc = load().hough_status(_ptr(_dev(st, "status", _torch().int32)), _stream(stream), ctypes.byref(flags))
+    if rc not in (OK, EDEVICE):
+        raise HoughError("hough_status", rc)
+    return int(flags.value)
+
+
+def resolve(p: Params) -> Params:
+    q = Params(*[getattr(p, n) for n, _ in Params._fields_])
+    _check("hough_resolve_params", load().hough_resolve_params(ctypes.byref(q)))
+    return q
+
+
+def workspace_size(p: Params, n_events: int) -> int:
+    return int(load().hough_workspace_size(ctypes.byref(p), int(n_events)))
+
+
+def workspace(p: Params, n_events: int, device="cuda"):
+    torch = _torch()
+    return torch.empty(workspace_size(p, n_events), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------- stepwise calls
+
+def map_hits(xy, off, st, uq=None, vq=None, stream=None):
+    torch = _torch()
+    xy = _dev(xy, "xy", torch.int32)
+    off = _dev(off, "off", torch.int64)
+    n = xy.shape[0]
+    uq = torch.empty(n, dtype=torch.int64, device=xy.device) if uq is None else _dev(uq, "uq", torch.int64)
+    vq = torch.empty(n, dtype=torch.int64, device=xy.device) if vq is None else _dev(vq, "vq", torch.int64)
+    _check("hough_map", load().hough_map(_ptr(xy), n, _ptr(off), off.shape[0] - 1, _ptr(uq), _ptr(vq), _ptr(st),
+                                         _stream(stream)))
+    return uq, vq
+
+
+def vote(uq, vq, off, p: Params, st, acc=None, stream=None):
+    torch = _torch()
+    ne = off.shape[0] - 1
+    if acc is None:
+        acc = torch.empty((ne, p.n_theta, p.n_rho), dtype=torch.int16, device=uq.device)
+    _check("hough_vote", load().hough_vote(_ptr(_dev(uq, "uq", torch.int64)), _ptr(_dev(vq, "vq", torch.int64)),
+                                           uq.shape[0], _ptr(_dev(off, "off", torch.int64)), ne, ctypes.byref(p),
+                                           _ptr(_dev(acc, "acc", torch.int16)), _ptr(st), _stream(stream)))
+    return acc
+
+
+def peaks(acc, p: Params, st, npeaks=None, pk=None, stream=None):
+    torch = _torch()
+    ne = acc.shape[0]
+    if npeaks is None:
+        npeaks = torch.zeros(ne, dtype=torch.int32, device=acc.device)
+    if pk is None:
+        pk = torch.zeros((ne, p.max_peaks, 4), dtype=torch.int16, device=acc.device)
+    _check("hough_peaks", load().hough_peaks(_ptr(_dev(acc, "acc", torch.int16)), ne, ctypes.byref(p),
+                                             _ptr(_dev(npeaks, "npeaks", torch.int32)),
+                                             _ptr(_dev(pk, "peaks", torch.int16)), _ptr(st), _stream(stream)))
+    return npeaks, pk
+
+
+def select(uq, vq, off, p: Params, npeaks, pk, st, mask=None, nkept=None, stream=None):
+    torch = _torch()
+    ne = off.shape[0] - 1
+    if mask is None:
+        mask = torch.empty(uq.shape[0], dtype=torch.uint8, device=uq.device)
+    if nkept is None:
+        nkept = torch.empty(ne, dtype=torch.int32, device=uq.device)
+    _check("hough_select", load().hough_select(
+        _ptr(_dev(uq, "uq", torch.int64)), _ptr(_dev(vq, "vq", torch.int64)), uq.shape[0],
+        _ptr(_dev(off, "off", torch.int64)), ne, ctypes.byref(p), _ptr(_dev(npeaks, "npeaks", torch.int32)),
+        _ptr(_dev(pk, "peaks", torch.int16)), _ptr(_dev(mask, "mask", torch.uint8)),
+        _ptr(_dev(nkept, "nkept", torch.int32)), _ptr(st), _stream(stream)))
+    return mask, nkept
+
+
+# ---------------------------------------------------------------- fused calls
+
+@dataclass
+class Outputs:
+    npeaks: "object"  # int32 [n_events]
+    peaks: "object"  # int16 [n_events, max_peaks, 4]: theta_bin, rho_bin, votes, flags
+    mask: "object"  # uint8 [n_hits]
+    nkept: "object"  # int32 [n_events]
+    checksum: "object"  # int64 view of uint64 [n_events], or None
+    ws: "object"
+    status: "object"
+
+
+def alloc_outputs(n_hits: int, n_events: int, p: Params, checksum: bool = False, device="cuda") -> Outputs:
+    torch = _torch()
+    return Outputs(
+        npeaks=torch.zeros(n_events, dtype=torch.int32, device=device),
+        peaks=torch.zeros((n_events, p.max_peaks, 4), dtype=torch.int16, device=device),
+        mask=torch.zeros(n_hits, dtype=torch.uint8, device=device),
+        nkept=torch.zeros(n_events, dtype=torch.int32, device=device),
+        checksum=torch.zeros(n_events, dtype=torch.int64, device=device) if checksum else None,
+        ws=workspace(p, n_events, device),
+        status=new_status(device),
+    )
+
+
+def run(xy, off, p: Params, out: Outputs | None = None, checksum: bool = False, batched: bool = False,
+        stream=None) -> Outputs:
+    """Whole path (map, rho, vote, peaks, select) in the fused kernel; ``batched`` uses the
+    persistent work-queue launch replayed as a CUDA graph."""
+    torch = _torch()
+    xy = _dev(xy, "xy", torch.int32)
+    off = _dev(off, "off", torch.int64)
+    ne = off.shape[0] - 1
+    if out is None:
+        out = alloc_outputs(xy.shape[0], ne, p, checksum, xy.device)
+    fn = load().hough_run_batched if batched else load().hough_run
+    rc = fn(_ptr(xy), xy.shape[0], _ptr(off), ne, ctypes.byref(p), _ptr(out.npeaks), _ptr(out.peaks), _ptr(out.mask),
+            _ptr(out.nkept), _ptr(out.checksum), _ptr(out.ws), out.ws.numel(), _ptr(out.status), _stream(stream))
+    _check("hough_run_batched" if batched else "hough_run", rc)
+    return out
+
+
+class HostRunner:
+    """End-to-end calls through ``hough_run_host``: host (pinned) inputs in, host results out,
+    every copy inside the call. Owns the device staging buffer and the pinned result buffers."""
+
+    def __init__(self, n_hits: int, n_events: int, p: Params, peaks_cap: int | None = None, device="cuda"):
+        torch = _torch()
+        self.p = p
+        self.n_hits, self.n_events = int(n_hits), int(n_events)
+        nbytes = int(load().hough_host_buffer_size(ctypes.byref(p), self.n_hits, self.n_events))
+        self.dbuf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.status = new_status(device)
+        cap = self.n_events * p.max_peaks if peaks_cap is None else int(peaks_cap)
+        self.npeaks = torch.zeros(self.n_events, dtype=torch.int32).pin_memory()
+        self.peak_off = torch.zeros(self.n_events + 1, dtype=torch.int64).pin_memory()
+        self.peaks = torch.zeros((max(cap, 1), 4), dtype=torch.int16).pin_memory()
+        self.mask = torch.zeros(max(self.n_hits, 1), dtype=torch.uint8).pin_memory()
+        self.nkept = torch.zeros(self.n_events, dtype=torch.int32).pin_memory()
+        self.cap = cap
+
+    def d2h_bytes(self) -> int:
+        """Bytes the last call copied back (results)."""
+        return 4 * self.n_events * 2 + 8 * (self.n_events + 1) + self.n_hits + 8 * int(self.peak_off[-1]) + 4
+
+    def __call__(self, xy_host, off_host, stream=None) -> int:
+        """Runs on pinned int32 [n_hits, 2] / int64 [n_events + 1] host tensors; returns the status flags."""
+        rc = load().hough_run_host(
+            ctypes.c_void_p(xy_host.data_ptr()), self.n_hits, ctypes.c_void_p(off_host.data_ptr()), self.n_events,
+            ctypes.byref(self.p), _ptr(self.npeaks), _ptr(self.peak_off), _ptr(self.peaks), self.cap,
+            _ptr(self.mask), _ptr(self.nkept), _ptr(self.dbuf), self.dbuf.numel(), _ptr(self.status), _stream(stream))
+        if rc == EDEVICE:
+            return int(self.status[0].item())
+        _check("hough_run_host", rc)
+        return 0
+
+
+def set_stage_events(begin=None, end=None):
+    """Records torch.cuda.Event pairs around the fused kernel of later calls on this thread."""
+    load().hough_set_stage_events(ctypes.c_void_p(begin.cuda_event) if begin is not None else None,
+                                  ctypes.c_void_p(end.cuda_event) if end is not None else None)
+
+
+def selftest_bin(n_rho: int, rho_lo: int, rho_hi: int, stream=None) -> int:
+    torch = _torch()
+    mism = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check("hough_selftest_bin", load().hough_selftest_bin(n_rho, rho_lo, rho_hi, _ptr(mism), _stream(stream)))
+    return mism
+
+
+def probe_smem_atomics(mode: int, ctas_per_sm: int, threads: int, smem_bytes: int, iters: int, sink, stream=None):
+    _check("hough_probe_smem_atomics", load().hough_probe_smem_atomics(mode, ctas_per_sm, threads, smem_bytes, iters,
+                                                                       _ptr(sink), _stream(stream)))

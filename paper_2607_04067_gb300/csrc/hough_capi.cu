@@ -1,0 +1,550 @@
+// C ABI of libhough.so: argument checks, launch planning, workspace layout, CUDA-graph
+// replay of the batched path, status words. See include/hough.h for the contract.
+#include <cmath>
+#include <cstring>
+#include <list>
+#include <mutex>
+
+#include "hough_internal.h"
+
+namespace hgpu {
+
+static thread_local int g_last_cuda = 0;
+static thread_local cudaEvent_t g_ev_begin = nullptr, g_ev_end = nullptr;
+
+static int cuda_fail(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return HOUGH_ECUDA;
+}
+
+// th_j = (j + 1/2) pi / N_theta; c_j = round(2^14 cos th_j) (half away from zero).
+void host_trig(int n_theta, TrigTable* t) {
+  std::memset(t, 0, sizeof(*t));
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j < n_theta; ++j) {
+    const double th = (j + 0.5) * pi / n_theta;
+    t->c[j] = (int16_t)std::llround(16384.0 * std::cos(th));
+    t->s[j] = (int16_t)std::llround(16384.0 * std::sin(th));
+  }
+}
+
+// M = ceil(2^64 N_rho / 2H), split into 32-bit halves (M < 2^44 for N_rho <= 1024).
+BinMagic host_magic(int n_rho) {
+  const unsigned __int128 two_h = (unsigned __int128)(2 * kH);
+  const unsigned __int128 num = ((unsigned __int128)1 << 64) * (unsigned __int128)n_rho;
+  const unsigned __int128 M = (num + two_h - 1) / two_h;
+  BinMagic m;
+  m.lo = (uint32_t)(M & 0xffffffffu);
+  m.hi = (uint32_t)(M >> 32);
+  return m;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(const Plan& pl, long long n_events) {
+  WsLayout w{};
+  size_t o = 0;
+  w.queue = o;
+  o = align256(o + 64);
+  const long long T = pl.tiles;
+  w.tickets = o;
+  if (T > 1) o = align256(o + 4 * (size_t)n_events);
+  w.tile_cnt = o;
+  if (T > 1) o = align256(o + 4 * (size_t)(n_events * T));
+  w.tile_cs = o;
+  if (T > 1) o = align256(o + 8 * (size_t)(n_events * T));
+  w.tile_peaks = o;
+  if (T > 1) o = align256(o + sizeof(hough_peak) * (size_t)(n_events * T) * (size_t)pl.max_peaks);
+  w.order = o;
+  o = align256(o + 4 * (size_t)(n_events > 0 ? n_events : 1));
+  w.total = o;
+  return w;
+}
+
+static constexpr int kSmemBudget = 227 * 1024 - 2048;  // dynamic bytes; static shared memory stays below 2 KB
+
+static int round16(int x) { return (x + 15) & ~15; }
+
+// Shared-memory layout for a shape; returns false if it does not fit.
+static bool layout(Plan& pl) {
+  const int wpad = pl.groups * 32;
+  const int cell = pl.acc32 ? 4 : 2;
+  const int acc_bytes = wpad * pl.nrho_pad * cell;
+  const int sel_bytes = (2 * pl.n_theta + 64) * 4 + pl.n_theta * 8 + pl.n_theta * pl.nrb * 4;
+  int o = 0;
+  pl.off_acc = o;
+  pl.region_bytes = round16(acc_bytes > sel_bytes ? acc_bytes : sel_bytes);
+  o += pl.region_bytes;
+  pl.off_halo = o;
+  if (pl.tiles > 1) o += round16(2 * pl.nrho_pad * 4);
+  pl.off_hits = o;
+  o += round16(pl.hit_cap * 8);
+  pl.off_pbits = o;
+  o += round16(wpad * pl.nrb * 4);
+  pl.off_cnt = o;
+  o += round16(wpad * pl.scan_ranges * 4);
+  pl.off_trig = o;
+  o += round16(2 * pl.n_theta * 2);
+  pl.smem_bytes = o;
+  return o <= kSmemBudget;
+}
+
+static int check_params(const hough_params* p) {
+  if (!p) return HOUGH_EINVAL;
+  if (p->n_theta < 4 || p->n_theta > 1024 || p->n_rho < 4 || p->n_rho > 1024) return HOUGH_EPARAM;
+  if (p->threshold < 1 || p->threshold > 32767) return HOUGH_EPARAM;
+  if (p->keep_halfwidth < 0 || p->keep_halfwidth > 1024) return HOUGH_EPARAM;
+  if (p->max_peaks < 1 || p->max_peaks > 65536) return HOUGH_EPARAM;
+  if (p->theta_tiles < 0 || p->theta_tiles > 64 || p->theta_tiles > p->n_theta) return HOUGH_EPARAM;
+  if (p->events_per_cta < 0 || p->events_per_cta > 1024) return HOUGH_EPARAM;
+  if (p->block < 0 || p->block > 1024 || (p->block % 32) != 0) return HOUGH_EPARAM;
+  return HOUGH_OK;
+}
+
+// Launch shape for parameters p; acc32 < 0 lets the planner choose the cell width.
+int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  std::memset(&pl, 0, sizeof(pl));
+  pl.n_theta = p->n_theta;
+  pl.n_rho = p->n_rho;
+  pl.threshold = p->threshold;
+  pl.keep_hw = p->keep_halfwidth;
+  pl.max_peaks = p->max_peaks;
+  pl.nrb = (p->n_rho + 31) / 32;
+  pl.magic = host_magic(p->n_rho);
+  pl.grab = p->events_per_cta > 0 ? p->events_per_cta : 1;
+  const int cell_choice = acc32 < 0 ? 0 : acc32;
+  for (int T = (p->theta_tiles ? p->theta_tiles : 1); T <= (p->theta_tiles ? p->theta_tiles : 64); ++T) {
+    const int W = (p->n_theta + T - 1) / T;
+    if ((T - 1) * W >= p->n_theta) continue;  // every tile must own at least one column
+    pl.tiles = T;
+    pl.tile_w = W;
+    pl.groups = (W + 31) / 32;
+    pl.acc32 = cell_choice;
+    pl.nrho_pad = pl.acc32 ? p->n_rho : ((p->n_rho + 1) & ~1);
+    const int halo = T > 1 ? 32 : 0;
+    if (p->block) {
+      const int work = p->block - halo;
+      if (work <= 0 || work % (pl.groups * 32)) return HOUGH_EPARAM;
+      pl.split = work / (pl.groups * 32);
+    } else {
+      int s = 512 / (pl.groups * 32);
+      if (s < 1) s = 1;
+      while (s > 1 && pl.groups * 32 * s + halo > 1024) --s;
+      pl.split = s;
+    }
+    pl.threads = pl.groups * 32 * pl.split + halo;
+    if (pl.threads > 1024) {
+      if (p->theta_tiles) return HOUGH_EPARAM;
+      continue;
+    }
+    int R = 4096 / (pl.groups * 32);
+    if (R < 1) R = 1;
+    if (R > 32) R = 32;
+    if (R > p->n_rho) R = p->n_rho;
+    pl.scan_ranges = R;
+    for (int cap = 4096; cap >= 512; cap >>= 1) {
+      pl.hit_cap = cap;
+      if (layout(pl)) return HOUGH_OK;
+    }
+    if (p->theta_tiles) return HOUGH_ESMEM;
+  }
+  return HOUGH_ESMEM;
+}
+
+// ---- CUDA graph cache of the batched path ----
+
+struct GraphKey {
+  const void *xy, *off, *npeaks, *peaks, *mask, *nkept, *checksum, *ws, *status;
+  long long n_hits, n_events;
+  size_t ws_bytes;
+  hough_params p;
+  cudaStream_t stream;
+  cudaEvent_t ev_begin, ev_end;
+  int device;
+  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+};
+
+static std::mutex g_graph_mu;
+static std::list<GraphEntry> g_graphs;
+
+}  // namespace hgpu
+
+using namespace hgpu;
+
+namespace {
+
+cudaError_t timed_fused(const Plan& pl, const FusedIO& io, const TrigTable& trig, int grid, cudaStream_t st) {
+  cudaError_t e;
+  if (g_ev_begin && g_ev_end) {
+    e = cudaEventRecord(g_ev_begin, st);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_fused(pl, io, trig, grid, st);
+  if (e == cudaSuccess && g_ev_begin && g_ev_end) e = cudaEventRecord(g_ev_end, st);
+  return e;
+}
+
+struct Common {
+  Plan pl;
+  WsLayout wl;
+  FusedIO io;
+};
+
+int prepare_fused(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, const hough_params* p,
+                  int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask, int32_t* d_nkept, uint64_t* d_checksum,
+                  void* d_ws, size_t ws_bytes, int32_t* d_status, Common& cm) {
+  if (!d_off || !d_npeaks || !d_peaks || !d_ws || !d_status || !d_nkept) return HOUGH_EINVAL;
+  if (n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
+  if (n_hits > 0 && (!d_xy || !d_mask)) return HOUGH_EINVAL;
+  if (((uintptr_t)d_xy & 7) || ((uintptr_t)d_ws & 255)) return HOUGH_EINVAL;
+  int rc = make_plan(p, cm.pl);
+  if (rc) return rc;
+  if ((long long)n_events * cm.pl.tiles > 0x7fffffffLL) return HOUGH_EINVAL;
+  cm.wl = ws_layout(cm.pl, n_events);
+  if (ws_bytes < cm.wl.total) return HOUGH_EWORKSPACE;
+  char* ws = (char*)d_ws;
+  FusedIO& io = cm.io;
+  std::memset(&io, 0, sizeof(io));
+  io.xy = (const int2*)d_xy;
+  io.n_hits = n_hits;
+  io.off = (const long long*)d_off;
+  io.n_events = n_events;
+  io.npeaks = d_npeaks;
+  io.peaks = d_peaks;
+  io.mask = d_mask;
+  io.nkept = d_nkept;
+  io.checksum = (unsigned long long*)d_checksum;
+  io.status = d_status;
+  io.queue = (unsigned long long*)(ws + cm.wl.queue);
+  io.tickets = cm.pl.tiles > 1 ? (int*)(ws + cm.wl.tickets) : nullptr;
+  io.tile_cnt = cm.pl.tiles > 1 ? (int*)(ws + cm.wl.tile_cnt) : nullptr;
+  io.tile_cs = cm.pl.tiles > 1 ? (unsigned long long*)(ws + cm.wl.tile_cs) : nullptr;
+  io.tile_peaks = cm.pl.tiles > 1 ? (hough_peak*)(ws + cm.wl.tile_peaks) : nullptr;
+  io.n_items = n_events * (long long)cm.pl.tiles;
+  return HOUGH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hough_map(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, int64_t* d_uq,
+              int64_t* d_vq, int32_t* d_status, void* stream) {
+  if (!d_off || !d_status || n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
+  if (n_hits > 0 && (!d_xy || !d_uq || !d_vq)) return HOUGH_EINVAL;
+  if ((uintptr_t)d_xy & 7) return HOUGH_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_prep((const long long*)d_off, n_events, n_hits, d_status, nullptr, nullptr, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (n_hits == 0) return HOUGH_OK;
+  e = launch_map((const int2*)d_xy, n_hits, (long long*)d_uq, (long long*)d_vq, d_status, st);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+int hough_vote(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+               const hough_params* p, int16_t* d_acc, int32_t* d_status, void* stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!d_off || !d_status || n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
+  if (n_events > 0 && !d_acc) return HOUGH_EINVAL;
+  if (n_hits > 0 && (!d_uq || !d_vq)) return HOUGH_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_prep((const long long*)d_off, n_events, n_hits, d_status, nullptr, nullptr, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  TrigTable trig;
+  host_trig(p->n_theta, &trig);
+  e = launch_vote((const long long*)d_uq, (const long long*)d_vq, (const long long*)d_off, n_events, *p, d_acc,
+                  d_status, trig, st);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+int hough_peaks(const int16_t* d_acc, int64_t n_events, const hough_params* p, int32_t* d_npeaks,
+                hough_peak* d_peaks, int32_t* d_status, void* stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!d_status || n_events < 0) return HOUGH_EINVAL;
+  if (n_events > 0 && (!d_acc || !d_npeaks || !d_peaks)) return HOUGH_EINVAL;
+  cudaError_t e = launch_peaks(d_acc, n_events, *p, d_npeaks, d_peaks, d_status, (cudaStream_t)stream);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+int hough_select(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                 const hough_params* p, const int32_t* d_npeaks, const hough_peak* d_peaks, uint8_t* d_mask,
+                 int32_t* d_nkept, int32_t* d_status, void* stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!d_off || !d_status || n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
+  if (n_events > 0 && (!d_npeaks || !d_peaks || !d_nkept)) return HOUGH_EINVAL;
+  if (n_hits > 0 && (!d_uq || !d_vq || !d_mask)) return HOUGH_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_prep((const long long*)d_off, n_events, n_hits, d_status, nullptr, nullptr, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  TrigTable trig;
+  host_trig(p->n_theta, &trig);
+  e = launch_select((const long long*)d_uq, (const long long*)d_vq, (const long long*)d_off, n_events, *p, d_npeaks,
+                    d_peaks, d_mask, d_nkept, d_status, trig, st);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+size_t hough_workspace_size(const hough_params* p, int64_t n_events) {
+  Plan pl;
+  if (make_plan(p, pl) != HOUGH_OK || n_events < 0) return 256;
+  return ws_layout(pl, n_events).total;
+}
+
+int hough_resolve_params(hough_params* p) {
+  Plan pl;
+  int rc = make_plan(p, pl);
+  if (rc) return rc;
+  p->theta_tiles = pl.tiles;
+  p->events_per_cta = pl.grab;
+  p->block = pl.threads;
+  return HOUGH_OK;
+}
+
+int hough_run(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, const hough_params* p,
+              int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask, int32_t* d_nkept, uint64_t* d_checksum,
+              void* d_ws, size_t ws_bytes, int32_t* d_status, void* stream) {
+  Common cm;
+  int rc = prepare_fused(d_xy, n_hits, d_off, n_events, p, d_npeaks, d_peaks, d_mask, d_nkept, d_checksum, d_ws,
+                         ws_bytes, d_status, cm);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_prep(cm.io.off, n_events, n_hits, d_status, cm.io.queue, cm.io.tickets, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (cm.io.n_items == 0) return HOUGH_OK;
+  TrigTable trig;
+  host_trig(p->n_theta, &trig);
+  cm.io.persistent = 0;
+  e = timed_fused(cm.pl, cm.io, trig, (int)cm.io.n_items, st);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+static int batched_grid(const Common& cm) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  const int per_sm = fused_max_ctas_per_sm(cm.pl);
+  if (per_sm < 1) return -1;
+  long long grid = (long long)sms * per_sm;
+  if (grid > cm.io.n_items) grid = cm.io.n_items;
+  return (int)(grid > 0 ? grid : 1);
+}
+
+static int enqueue_batched(const Common& cm0, const hough_params* p, int64_t n_hits, int64_t n_events, void* d_ws,
+                           int32_t* d_status, int grid, cudaStream_t st) {
+  Common cm = cm0;
+  int* order = (int*)((char*)d_ws + cm.wl.order);
+  cudaError_t e = launch_prep(cm.io.off, n_events, n_hits, d_status, cm.io.queue, cm.io.tickets, order, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (cm.io.n_items == 0) return HOUGH_OK;
+  TrigTable trig;
+  host_trig(p->n_theta, &trig);
+  cm.io.order = order;
+  cm.io.persistent = 1;
+  e = timed_fused(cm.pl, cm.io, trig, grid, st);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+int hough_run_batched(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                      const hough_params* p, int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask,
+                      int32_t* d_nkept, uint64_t* d_checksum, void* d_ws, size_t ws_bytes, int32_t* d_status,
+                      void* stream) {
+  Common cm;
+  int rc = prepare_fused(d_xy, n_hits, d_off, n_events, p, d_npeaks, d_peaks, d_mask, d_nkept, d_checksum, d_ws,
+                         ws_bytes, d_status, cm);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = batched_grid(cm);
+  if (grid < 1) return HOUGH_ESMEM;
+  if (st == nullptr) return enqueue_batched(cm, p, n_hits, n_events, d_ws, d_status, grid, st);  // legacy stream: no capture
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.xy = d_xy;
+  key.off = d_off;
+  key.npeaks = d_npeaks;
+  key.peaks = d_peaks;
+  key.mask = d_mask;
+  key.nkept = d_nkept;
+  key.checksum = d_checksum;
+  key.ws = d_ws;
+  key.status = d_status;
+  key.n_hits = n_hits;
+  key.n_events = n_events;
+  key.ws_bytes = ws_bytes;
+  key.p = *p;
+  key.stream = st;
+  key.ev_begin = g_ev_begin;
+  key.ev_end = g_ev_end;
+  cudaGetDevice(&key.device);
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+    if (it->key == key) {
+      g_graphs.splice(g_graphs.begin(), g_graphs, it);
+      cudaError_t e = cudaGraphLaunch(it->exec, st);
+      return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e);
+  rc = enqueue_batched(cm, p, n_hits, n_events, d_ws, d_status, grid, st);
+  e = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e);
+  g_graphs.push_front(GraphEntry{key, exec});
+  while (g_graphs.size() > 16) {
+    cudaGraphExecDestroy(g_graphs.back().exec);
+    g_graphs.pop_back();
+  }
+  e = cudaGraphLaunch(exec, st);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+void hough_set_stage_events(void* begin, void* end) {
+  g_ev_begin = (begin && end) ? (cudaEvent_t)begin : nullptr;
+  g_ev_end = (begin && end) ? (cudaEvent_t)end : nullptr;
+}
+
+namespace {
+struct HostLayout {
+  size_t xy, off, npeaks, peaks, mask, nkept, peak_off, dense, ws, ws_bytes, total;
+};
+
+bool host_layout(const hough_params* p, int64_t n_hits, int64_t n_events, HostLayout& L) {
+  Plan pl;
+  if (make_plan(p, pl) != HOUGH_OK || n_hits < 0 || n_events < 0) return false;
+  const size_t ne = (size_t)n_events, nh = (size_t)n_hits, mp = (size_t)p->max_peaks;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = (o + (bytes ? bytes : 1) + 255) & ~(size_t)255;
+    return at;
+  };
+  L.xy = take(8 * nh);
+  L.off = take(8 * (ne + 1));
+  L.npeaks = take(4 * ne);
+  L.peaks = take(sizeof(hough_peak) * ne * mp);
+  L.mask = take(nh);
+  L.nkept = take(4 * ne);
+  L.peak_off = take(8 * (ne + 1));
+  L.dense = take(sizeof(hough_peak) * ne * mp);
+  L.ws_bytes = ws_layout(pl, n_events).total;
+  L.ws = take(L.ws_bytes);
+  L.total = o;
+  return true;
+}
+}  // namespace
+
+size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_events) {
+  HostLayout L;
+  return host_layout(p, n_hits, n_events, L) ? L.total : 256;
+}
+
+int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, int64_t n_events, const hough_params* p,
+                   int32_t* h_npeaks, int64_t* h_peak_off, hough_peak* h_peaks, int64_t h_peaks_cap, uint8_t* h_mask,
+                   int32_t* h_nkept, void* d_buf, size_t d_buf_bytes, int32_t* d_status, void* stream) {
+  if (!h_off || !h_npeaks || !h_peak_off || !h_nkept || !d_buf || !d_status || n_hits < 0 || n_events < 0 ||
+      h_peaks_cap < 0)
+    return HOUGH_EINVAL;
+  if (n_hits > 0 && (!h_xy || !h_mask)) return HOUGH_EINVAL;
+  if (h_peaks_cap > 0 && !h_peaks) return HOUGH_EINVAL;
+  if ((uintptr_t)d_buf & 255) return HOUGH_EINVAL;
+  int rc = check_params(p);
+  if (rc) return rc;
+  HostLayout L;
+  if (!host_layout(p, n_hits, n_events, L)) return HOUGH_EPARAM;
+  if (d_buf_bytes < L.total) return HOUGH_EWORKSPACE;
+  char* b = (char*)d_buf;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ne = (size_t)n_events, nh = (size_t)n_hits;
+  cudaError_t e = cudaMemcpyAsync(b + L.xy, h_xy, 8 * nh, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + L.off, h_off, 8 * (ne + 1), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  rc = hough_run_batched((const int32_t*)(b + L.xy), n_hits, (const int64_t*)(b + L.off), n_events, p,
+                         (int32_t*)(b + L.npeaks), (hough_peak*)(b + L.peaks), (uint8_t*)(b + L.mask),
+                         (int32_t*)(b + L.nkept), nullptr, b + L.ws, L.ws_bytes, d_status, stream);
+  if (rc) return rc;
+  e = launch_pack_peaks((const int*)(b + L.npeaks), (const hough_peak*)(b + L.peaks), n_events, p->max_peaks,
+                        (long long*)(b + L.peak_off), (hough_peak*)(b + L.dense), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_npeaks, b + L.npeaks, 4 * ne, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_nkept, b + L.nkept, 4 * ne, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && nh) e = cudaMemcpyAsync(h_mask, b + L.mask, nh, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_peak_off, b + L.peak_off, 8 * (ne + 1), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int64_t total = h_peak_off[ne];
+  if (total > h_peaks_cap) return HOUGH_EWORKSPACE;
+  if (total > 0) {
+    e = cudaMemcpyAsync(h_peaks, b + L.dense, sizeof(hough_peak) * (size_t)total, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  int32_t flags = 0;
+  e = cudaMemcpyAsync(&flags, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return flags ? HOUGH_EDEVICE : HOUGH_OK;
+}
+
+int hough_status(const int32_t* d_status, void* stream, int32_t* host_flags) {
+  if (!d_status || !host_flags) return HOUGH_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemcpy(host_flags, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return *host_flags ? HOUGH_EDEVICE : HOUGH_OK;
+}
+
+const char* hough_strerror(int code) {
+  switch (code) {
+    case HOUGH_OK: return "ok";
+    case HOUGH_EINVAL: return "invalid argument (null pointer, negative count or misaligned buffer)";
+    case HOUGH_EPARAM: return "parameters out of range";
+    case HOUGH_ESMEM: return "shape does not fit shared memory";
+    case HOUGH_ECUDA: return "CUDA runtime error";
+    case HOUGH_EWORKSPACE: return "workspace too small";
+    case HOUGH_ETIMEDOUT: return "bounded wait timed out";
+    case HOUGH_EFULL: return "no free serving slot";
+    case HOUGH_EDEVICE: return "device status flags set";
+    case HOUGH_F_BAD_HIT: return "hit at r = 0 or beyond 2^24 um";
+    case HOUGH_F_BAD_OFFSETS: return "event offsets invalid";
+    case HOUGH_F_PEAK_OVERFLOW: return "more peaks than max_peaks";
+    case HOUGH_F_EVENT_TOO_LARGE: return "event has more than HOUGH_MAX_EVENT_HITS hits";
+    case HOUGH_F_TIMEOUT: return "device wait timed out";
+    default: return "unknown code";
+  }
+}
+
+int hough_last_cuda_error(void) { return g_last_cuda; }
+
+int hough_selftest_bin(int32_t n_rho, int64_t rho_lo, int64_t rho_hi, unsigned long long* d_mismatch,
+                       void* stream) {
+  if (!d_mismatch || n_rho < 4 || n_rho > 1024 || rho_hi < rho_lo) return HOUGH_EINVAL;
+  cudaError_t e = launch_selftest_bin(n_rho, rho_lo, rho_hi, d_mismatch, (cudaStream_t)stream);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,
+                             unsigned long long* d_sink, void* stream) {
+  if (!d_sink || mode < 0 || mode > 2 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads % 32) ||
+      smem_bytes < 4096 || smem_bytes > kSmemBudget || iters < 1)
+    return HOUGH_EINVAL;
+  cudaError_t e = launch_probe_atomics(mode, ctas_per_sm, threads, smem_bytes, iters, d_sink, (cudaStream_t)stream);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Library-internal declarations shared by the kernel files and the C ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hough.h"
+#include "hough_device.cuh"
+
+namespace hgpu {
+
+// Launch shape and shared-memory layout of the fused kernel for one parameter set.
+struct Plan {
+  int n_theta, n_rho, threshold, keep_hw, max_peaks;
+  int tiles;      // theta tiles per event
+  int tile_w;     // columns per tile (last tile may be narrower)
+  int groups;     // 32-column groups per tile
+  int split;      // warps voting each column group (hit partitions)
+  int threads;    // CTA size: groups * split * 32 (+ 32 halo lanes when tiles > 1)
+  int acc32;      // 1: one int32 cell per shared word; 0: two int16 cells per word
+  int nrho_pad;   // rows allocated per column
+  int nrb;        // 32-bit bitmap words per column
+  int hit_cap;    // hits staged in shared memory per chunk
+  int scan_ranges;  // row ranges of the peak scan
+  int grab;       // persistent queue: items per pop
+  int ctas_per_sm;
+  // shared-memory layout in bytes
+  int off_acc, region_bytes, off_halo, off_hits, off_pbits, off_cnt, off_trig, smem_bytes;
+  BinMagic magic;
+};
+
+struct FusedIO {
+  const int2* xy;
+  long long n_hits;
+  const long long* off;
+  long long n_events;
+  int* npeaks;
+  hough_peak* peaks;
+  uint8_t* mask;
+  int* nkept;
+  unsigned long long* checksum;  // nullable
+  int* status;                   // [0] sticky flags, [1] per-call offsets flag
+  unsigned long long* queue;     // persistent item counter
+  const int* order;              // nullable: events in processing order
+  int* tickets;                  // per event, tiles > 1
+  int* tile_cnt;                 // [n_events * tiles]
+  unsigned long long* tile_cs;   // [n_events * tiles]
+  hough_peak* tile_peaks;        // [n_events * tiles * max_peaks]
+  long long n_items;
+  int persistent;
+};
+
+// Workspace carve-up (byte offsets inside the caller's buffer).
+struct WsLayout {
+  size_t queue, tickets, tile_cnt, tile_cs, tile_peaks, order, total;
+};
+
+WsLayout ws_layout(const Plan& pl, long long n_events);
+void host_trig(int n_theta, TrigTable* t);
+BinMagic host_magic(int n_rho);
+
+cudaError_t launch_prep(const long long* off, long long n_events, long long n_hits, int* status,
+                        unsigned long long* queue, int* tickets, int* order, cudaStream_t st);
+cudaError_t launch_fused(const Plan& pl, const FusedIO& io, const TrigTable& trig, int grid, cudaStream_t st);
+int fused_max_ctas_per_sm(const Plan& pl);
+
+cudaError_t launch_map(const int2* xy, long long n_hits, long long* uq, long long* vq, int* status, cudaStream_t st);
+cudaError_t launch_vote(const long long* uq, const long long* vq, const long long* off, long long n_events,
+                        const hough_params& p, int16_t* acc, int* status, const TrigTable& trig, cudaStream_t st);
+cudaError_t launch_peaks(const int16_t* acc, long long n_events, const hough_params& p, int* npeaks,
+                         hough_peak* peaks, int* status, cudaStream_t st);
+cudaError_t launch_select(const long long* uq, const long long* vq, const long long* off, long long n_events,
+                          const hough_params& p, const int* npeaks, const hough_peak* peaks, uint8_t* mask,
+                          int* nkept, int* status, const TrigTable& trig, cudaStream_t st);
+
+cudaError_t launch_pack_peaks(const int* npeaks, const hough_peak* peaks, long long n_events, int max_peaks,
+                              long long* peak_off, hough_peak* dense, cudaStream_t st);
+
+cudaError_t launch_selftest_bin(int n_rho, long long lo, long long hi, unsigned long long* mismatch, cudaStream_t st);
+cudaError_t launch_probe_atomics(int mode, int ctas_per_sm, int threads, int smem_bytes, int iters,
+                                 unsigned long long* sink, cudaStream_t st);
+
+}  // namespace hgpu

@@ -1,0 +1,322 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Integer path, so the bar is bit-exact equality of accumulators, peak lists, masks,
+kept counts and accumulator checksums.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from parity_util import assert_event_outputs_equal, peaks_np, sub_batch, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_04067_gb300 as hough
+    hough.load()
+    return hough
+
+
+def cfg_params(h, cfg, **kw):
+    return h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks, **kw)
+
+
+def dev(ev):
+    return torch.from_numpy(ev.xy).cuda(), torch.from_numpy(ev.off).cuda()
+
+
+def oracle_of(cfg, ev, with_acc=False, max_peaks=None, **kw):
+    p = oracle.params(kw.get("n_theta", cfg.n_theta), kw.get("n_rho", cfg.n_rho), kw.get("threshold", cfg.threshold),
+                      kw.get("keep_halfwidth", cfg.keep_halfwidth), max_peaks or cfg.max_peaks)
+    return oracle.run(ev.xy, ev.off, p, with_acc=with_acc, threads=THREADS)
+
+
+# ---------------------------------------------------------------- stepwise path
+
+def test_stepwise_matches_oracle(h):
+    cfg = gen.CONFIGS["plain_small"]
+    ev = gen.generate(cfg)
+    ref = oracle_of(cfg, ev, with_acc=True)
+    xy, off = dev(ev)
+    p = cfg_params(h, cfg)
+    st = h.new_status()
+    uq, vq = h.map_hits(xy, off, st)
+    exp_u = np.array([oracle.map_hit(x, y)[1] for x, y in ev.xy[:2000]])
+    exp_v = np.array([oracle.map_hit(x, y)[2] for x, y in ev.xy[:2000]])
+    assert np.array_equal(to_np(uq)[:2000], exp_u) and np.array_equal(to_np(vq)[:2000], exp_v)
+    acc = h.vote(uq, vq, off, p, st)
+    assert np.array_equal(to_np(acc), ref.acc)
+    npk, pk = h.peaks(acc, p, st)
+    mask, nkept = h.select(uq, vq, off, p, npk, pk, st)
+    assert h.status(st) == 0
+    assert_event_outputs_equal(ref, npk, pk, mask, nkept, ev.off)
+
+
+def test_stepwise_vote_tiled_large_accumulator(h):
+    cfg = gen.CONFIGS["stress"]
+    ev = gen.generate(cfg, 6)
+    ref = oracle_of(cfg, ev, with_acc=True)
+    xy, off = dev(ev)
+    p = cfg_params(h, cfg)
+    st = h.new_status()
+    uq, vq = h.map_hits(xy, off, st)
+    acc = h.vote(uq, vq, off, p, st)
+    assert np.array_equal(to_np(acc), ref.acc)
+    npk, pk = h.peaks(acc, p, st)
+    mask, nkept = h.select(uq, vq, off, p, npk, pk, st)
+    assert h.status(st) == 0
+    assert_event_outputs_equal(ref, npk, pk, mask, nkept, ev.off)
+
+
+# ---------------------------------------------------------------- fused path
+
+@pytest.mark.parametrize("name,n", [("plain_small", None), ("plain_paper", None), ("batched", 400), ("stress", 24)])
+@pytest.mark.parametrize("batched", [False, True])
+def test_fused_matches_oracle(h, name, n, batched):
+    cfg = gen.CONFIGS[name]
+    ev = gen.generate(cfg, n)
+    ref = oracle_of(cfg, ev)
+    xy, off = dev(ev)
+    out = h.run(xy, off, cfg_params(h, cfg), checksum=True, batched=batched)
+    assert h.status(out.status) == 0
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, checksum=out.checksum)
+
+
+@pytest.mark.parametrize("n_theta,n_rho,tiles,block", [
+    (256, 256, 2, 0), (256, 256, 4, 0), (256, 256, 8, 0), (256, 256, 1, 256), (256, 256, 1, 1024),
+    (256, 256, 3, 0), (64, 64, 2, 0), (64, 64, 1, 64), (100, 63, 1, 0), (100, 63, 3, 0), (4, 4, 1, 0),
+    (1024, 1024, 0, 0), (1000, 1000, 0, 0), (37, 257, 2, 0)])
+def test_shapes_and_tiles(h, n_theta, n_rho, tiles, block):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 40)
+    thr = max(2, cfg.threshold * min(n_theta, n_rho) // 256)
+    ref = oracle.run(ev.xy, ev.off, oracle.params(n_theta, n_rho, thr, 1, 4096), threads=THREADS)
+    xy, off = dev(ev)
+    for batched in (False, True):
+        out = h.run(xy, off, h.params(n_theta, n_rho, thr, 1, 4096, theta_tiles=tiles, block=block), checksum=True,
+                    batched=batched)
+        assert h.status(out.status) == 0
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, checksum=out.checksum)
+
+
+def test_checksum_off_gives_same_results(h):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 50)
+    xy, off = dev(ev)
+    a = h.run(xy, off, cfg_params(h, cfg), checksum=True, batched=True)
+    b = h.run(xy, off, cfg_params(h, cfg), checksum=False, batched=True)
+    assert torch.equal(a.mask, b.mask) and torch.equal(a.npeaks, b.npeaks) and torch.equal(a.nkept, b.nkept)
+    assert np.array_equal(peaks_np(a.peaks), peaks_np(b.peaks))
+
+
+# ---------------------------------------------------------------- full-size workloads, sampled
+
+@pytest.mark.parametrize("name,sample", [("batched", 300), ("stress", 60)])
+def test_full_size_sampled(h, name, sample):
+    """Whole workload in the launch configuration the benchmark times (batched, no checksum),
+    then the oracle recomputes a random sample of events one by one."""
+    cfg = gen.CONFIGS[name]
+    ev = gen.generate(cfg, with_truth=False)
+    xy, off = dev(ev)
+    p = cfg_params(h, cfg)
+    out = h.run(xy, off, p, checksum=False, batched=True)
+    assert h.status(out.status) == 0
+    rng = np.random.default_rng(1)
+    events = np.sort(rng.choice(ev.n_events, size=sample, replace=False))
+    events[0] = 0
+    events[-1] = ev.n_events - 1
+    sxy, soff = sub_batch(ev.xy, ev.off, events)
+    ref = oracle.run(sxy, soff, oracle.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth,
+                                              cfg.max_peaks), threads=THREADS)
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, events=events)
+    # properties over every event
+    nk = to_np(out.nkept)
+    m = to_np(out.mask)
+    per_event = np.add.reduceat(m.astype(np.int64), ev.off[:-1]) if ev.n_hits else np.zeros(0)
+    per_event[np.diff(ev.off) == 0] = 0
+    assert np.array_equal(per_event, nk)
+    assert np.all(to_np(out.npeaks) <= cfg.max_peaks)
+    assert set(np.unique(m)) <= {0, 1}
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_batch_and_empty_events(h):
+    p = h.params(64, 64, 2)
+    xy = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for batched in (False, True):
+        out = h.run(xy, off, p, batched=batched)
+        assert h.status(out.status) == 0
+    ev = gen.generate("plain_small", 5)
+    parts = [gen.Events(np.zeros((0, 2), np.int32), np.zeros(1, np.int64), None), ev,
+             gen.Events(np.zeros((0, 2), np.int32), np.zeros(2, np.int64), None)]
+    cat = gen.concat(parts)
+    ref = oracle.run(cat.xy, cat.off, oracle.params(64, 64, 12), threads=THREADS)
+    xy, off = dev(cat)
+    for batched in (False, True):
+        out = h.run(xy, off, h.params(64, 64, 12), checksum=True, batched=batched)
+        assert h.status(out.status) == 0
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, cat.off, checksum=out.checksum)
+
+
+def test_bad_hits_and_small_radii(h):
+    """r = 0 and out-of-range hits are skipped and flagged; hits inside r ~ 195 mm take the
+    int64 path (rho clamped to the edge bins)."""
+    rng = np.random.default_rng(9)
+    ev = gen.generate("plain_paper", 30)
+    xy = ev.xy.copy()
+    idx = rng.choice(len(xy), 60, replace=False)
+    xy[idx[:10]] = 0
+    xy[idx[10:15], 0] = 2 ** 24 + 5
+    small = rng.integers(-150000, 150000, size=(45, 2)).astype(np.int32)
+    xy[idx[15:]] = small
+    ref = oracle.run(xy, ev.off, oracle.params(256, 256, 16, 1, 4096), threads=THREADS)
+    assert ref.status == oracle.F_BAD_HIT
+    t_xy, off = torch.from_numpy(xy).cuda(), torch.from_numpy(ev.off).cuda()
+    for batched in (False, True):
+        for tiles in (1, 2):
+            out = h.run(t_xy, off, h.params(256, 256, 16, 1, 4096, theta_tiles=tiles), checksum=True, batched=batched)
+            assert h.status(out.status) == h.F_BAD_HIT
+            assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off,
+                                       checksum=out.checksum)
+    st = h.new_status()
+    uq, vq = h.map_hits(t_xy, off, st)
+    assert h.status(st) == h.F_BAD_HIT
+    u = to_np(uq)
+    assert np.all(u[idx[:15]] == np.iinfo(np.int64).min)
+
+
+def test_all_hits_small_radius_event(h):
+    """Every hit on the int64 path, across several staging chunks."""
+    rng = np.random.default_rng(4)
+    xy = rng.integers(-190000, 190000, size=(9000, 2)).astype(np.int32)
+    xy[np.all(xy == 0, axis=1)] = 1
+    off = np.array([0, 3000, 9000], np.int64)
+    ref = oracle.run(xy, off, oracle.params(128, 128, 40, 1, 8192), threads=THREADS)
+    t_xy, t_off = torch.from_numpy(xy).cuda(), torch.from_numpy(off).cuda()
+    for tiles in (1, 2):
+        out = h.run(t_xy, t_off, h.params(128, 128, 40, 1, 8192, theta_tiles=tiles), checksum=True, batched=True)
+        assert h.status(out.status) == 0
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, off, checksum=out.checksum)
+
+
+def test_large_event_chunks_and_too_large(h):
+    """An event bigger than one staging chunk, and one above 32767 hits (skipped, flagged)."""
+    ev = gen.generate("stress", 8)
+    big = np.tile(ev.xy, (1, 1))[:32767]
+    huge = np.concatenate([ev.xy] * 2)[:32768]
+    xy = np.concatenate([big, huge, ev.xy[:500]])
+    off = np.array([0, len(big), len(big) + len(huge), len(xy)], np.int64)
+    ref = oracle.run(xy, off, oracle.params(256, 256, 200, 1, 4096), threads=THREADS)
+    assert ref.status == oracle.F_EVENT_TOO_LARGE
+    t_xy, t_off = torch.from_numpy(xy).cuda(), torch.from_numpy(off).cuda()
+    for tiles in (1, 4):
+        out = h.run(t_xy, t_off, h.params(256, 256, 200, 1, 4096, theta_tiles=tiles), checksum=True, batched=True)
+        assert h.status(out.status) == h.F_EVENT_TOO_LARGE
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, off, checksum=out.checksum)
+
+
+def test_bad_offsets_write_nothing(h):
+    ev = gen.generate("plain_small", 10)
+    bad = ev.off.copy()
+    bad[3], bad[4] = bad[4], bad[3]
+    xy, off = torch.from_numpy(ev.xy).cuda(), torch.from_numpy(bad).cuda()
+    for batched in (False, True):
+        out = h.run(xy, off, h.params(64, 64, 12), batched=batched)
+        out.npeaks.fill_(-7)
+        out.status.zero_()
+        h.run(xy, off, h.params(64, 64, 12), out=out, batched=batched)
+        assert h.status(out.status) == h.F_BAD_OFFSETS
+        assert torch.all(out.npeaks == -7)
+    st = h.new_status()
+    h.map_hits(xy, off, st)
+    assert h.status(st) == h.F_BAD_OFFSETS
+
+
+def test_peak_overflow_keeps_first_in_raster_order(h):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 20)
+    ref = oracle.run(ev.xy, ev.off, oracle.params(256, 256, 16, 1, 100), threads=THREADS)
+    assert ref.status == oracle.F_PEAK_OVERFLOW
+    xy, off = dev(ev)
+    for tiles in (1, 2, 4):
+        out = h.run(xy, off, h.params(256, 256, 16, 1, 100, theta_tiles=tiles), batched=True)
+        assert h.status(out.status) == h.F_PEAK_OVERFLOW
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off)
+
+
+@pytest.mark.parametrize("hw", [0, 3])
+def test_keep_halfwidth(h, hw):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 30)
+    ref = oracle.run(ev.xy, ev.off, oracle.params(256, 256, 16, hw, 4096), threads=THREADS)
+    xy, off = dev(ev)
+    out = h.run(xy, off, h.params(256, 256, 16, hw, 4096), batched=True)
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off)
+
+
+def test_permutation_invariance_on_gpu(h):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 20)
+    rng = np.random.default_rng(2)
+    perm = np.concatenate([ev.off[e] + rng.permutation(ev.off[e + 1] - ev.off[e]) for e in range(20)])
+    xy, off = dev(ev)
+    a = h.run(xy, off, cfg_params(h, cfg), checksum=True, batched=True)
+    b = h.run(torch.from_numpy(ev.xy[perm]).cuda(), off, cfg_params(h, cfg), checksum=True, batched=True)
+    assert torch.equal(a.npeaks, b.npeaks) and torch.equal(a.checksum, b.checksum)
+    assert np.array_equal(peaks_np(a.peaks), peaks_np(b.peaks))
+    assert np.array_equal(to_np(a.mask)[perm], to_np(b.mask))
+
+
+def test_non_default_stream_and_graph_replay(h):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 64)
+    ref = oracle_of(cfg, ev)
+    xy, off = dev(ev)
+    s = torch.cuda.Stream()
+    out = h.alloc_outputs(ev.n_hits, ev.n_events, cfg_params(h, cfg), checksum=True)
+    torch.cuda.synchronize()
+    for _ in range(3):  # the second and third calls replay the cached graph
+        out.mask.fill_(7)
+        with torch.cuda.stream(s):
+            h.run(xy, off, cfg_params(h, cfg), out=out, batched=True, stream=s)
+        s.synchronize()
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, checksum=out.checksum)
+
+
+# ---------------------------------------------------------------- exhaustive bin function
+
+@pytest.mark.parametrize("n_rho", [4, 63, 64, 256, 512, 1000, 1024])
+def test_bin_function_exhaustive(h, n_rho):
+    """Every rho in [-H - 10^6, H + 10^6]: the device's multiply-high binning equals plain
+    64-bit floor division with clamping."""
+    H = 703687442
+    m = h.selftest_bin(n_rho, -H - 10 ** 6, H + 10 ** 6)
+    assert int(m.item()) == 0
+
+
+def test_host_errors(h):
+    xy = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
+    off = torch.tensor([0, 4], dtype=torch.int64, device="cuda")
+    for bad in (h.params(3, 64, 2), h.params(64, 1025, 2), h.params(64, 64, 0), h.params(64, 64, 2, max_peaks=0),
+                h.params(64, 64, 2, block=48), h.params(64, 64, 2, theta_tiles=65)):
+        with pytest.raises(h.HoughError) as ei:
+            h.run(xy, off, bad, out=h.alloc_outputs(4, 1, h.params(64, 64, 2)))
+        assert ei.value.code == h.EPARAM
+    p = h.params(64, 64, 2)
+    out = h.alloc_outputs(4, 1, p)
+    out.ws = out.ws[:16]
+    with pytest.raises(h.HoughError) as ei:
+        h.run(xy, off, p, out=out)
+    assert ei.value.code == h.EWORKSPACE
