@@ -217,6 +217,9 @@ def main():
     out = h.alloc_outputs(ev.n_hits, ev.n_events, p)
     stream = torch.cuda.Stream()
     pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+    for b_, e_ in pairs:  # torch only reports elapsed time for events it has recorded once itself;
+        b_.record(stream)  # later records of the same native events are made by the library
+        e_.record(stream)
 
     def step(i):
         h.set_stage_events(*pairs[i % 2])

@@ -182,12 +182,13 @@ namespace {
 
 cudaError_t timed_fused(const Plan& pl, const FusedIO& io, const TrigTable& trig, int grid, cudaStream_t st) {
   cudaError_t e;
+  // External records become real event-record nodes when the stream is being captured.
   if (g_ev_begin && g_ev_end) {
-    e = cudaEventRecord(g_ev_begin, st);
+    e = cudaEventRecordWithFlags(g_ev_begin, st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
   }
   e = launch_fused(pl, io, trig, grid, st);
-  if (e == cudaSuccess && g_ev_begin && g_ev_end) e = cudaEventRecord(g_ev_end, st);
+  if (e == cudaSuccess && g_ev_begin && g_ev_end) e = cudaEventRecordWithFlags(g_ev_end, st, cudaEventRecordExternal);
   return e;
 }
 
@@ -200,8 +201,9 @@ struct Common {
 int prepare_fused(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, const hough_params* p,
                   int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask, int32_t* d_nkept, uint64_t* d_checksum,
                   void* d_ws, size_t ws_bytes, int32_t* d_status, Common& cm) {
-  if (!d_off || !d_npeaks || !d_peaks || !d_ws || !d_status || !d_nkept) return HOUGH_EINVAL;
+  if (!d_off || !d_ws || !d_status) return HOUGH_EINVAL;
   if (n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
+  if (n_events > 0 && (!d_npeaks || !d_peaks || !d_nkept)) return HOUGH_EINVAL;
   if (n_hits > 0 && (!d_xy || !d_mask)) return HOUGH_EINVAL;
   if (((uintptr_t)d_xy & 7) || ((uintptr_t)d_ws & 255)) return HOUGH_EINVAL;
   int rc = make_plan(p, cm.pl);

@@ -14,9 +14,9 @@
 //     (halo), so the 3x3 peak test is exact on tile edges; the last tile CTA of an
 //     event (ticket counter) merges the tiles' peak lists in tile order and selects.
 #include <climits>
+#include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
+#include <utility>
 
 #include "hough_internal.h"
 
@@ -657,6 +657,7 @@ __global__ void __launch_bounds__(1024) fused_kernel(const Plan pl, const FusedI
     tc[j] = trig.c[j];
     tc[pl.n_theta + j] = trig.s[j];
   }
+  __syncthreads();  // the table is read before run_item's first barrier
   const bool do_cs = io.checksum != nullptr;
   if (!io.persistent) {
     run_item<A32>(pl, io, smem, sh, blockIdx.x, do_cs);
@@ -718,18 +719,19 @@ cudaError_t launch_prep(const long long* off, long long n_events, long long n_hi
   return cudaGetLastError();
 }
 
-// Raises the kernel's dynamic shared-memory limit once per (kernel, size, device), so that
-// no attribute call happens while a stream is being captured into a graph.
+// Raises the kernel's dynamic shared-memory limit to the largest size requested so far
+// (per kernel and device; never lowers it), so that no attribute call happens while a
+// stream is being captured into a graph once a shape has been used.
 static cudaError_t set_smem(const void* fn, int bytes) {
   static std::mutex mu;
-  static std::set<std::tuple<const void*, int, int>> done;
+  static std::map<std::pair<const void*, int>, int> limit;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_tuple(fn, bytes, dev);
-  if (done.count(key)) return cudaSuccess;
+  int& cur = limit[std::make_pair(fn, dev)];
+  if (bytes <= cur) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.insert(key);
+  if (e == cudaSuccess) cur = bytes;
   return e;
 }
 
