@@ -167,6 +167,27 @@ size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_e
  * with cudaEventElapsedTime. NULL, NULL turns it off. Graph replays are cached per pair. */
 void hough_set_stage_events(void* begin, void* end);
 
+/* Size of the library's built-in scratch array used by hough_run_batched_static. */
+#define HOUGH_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* hough_run_batched for callers that cannot allocate device memory (the paper has no
+ * counterpart; it is an interface convenience). Examples: a plain-C trigger process whose
+ * only device buffers are the input and output buffers its readout layer mapped once, or a
+ * real-time loop that must not call cudaMalloc after start-up because an allocation can
+ * synchronise the device. The caller passes inputs and outputs exactly as for
+ * hough_run_batched but no workspace: the scratch (queue counter, event order, tile peak
+ * slots) comes from a HOUGH_STATIC_SCRATCH_BYTES array compiled into the library, which
+ * every GPU that loads the library keeps until the process exits. Batches whose scratch,
+ * hough_workspace_size(p, n_events), exceeds that size are rejected with HOUGH_EWORKSPACE.
+ * The call allocates nothing. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current), so make that first call before
+ * any stream capture. All calls share the one array: calls that can overlap on the GPU (on
+ * different streams or host threads) race and must be serialised by the caller. Results are
+ * identical to hough_run_batched (the same kernels run, launched directly, without a graph). */
+int hough_run_batched_static(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                             const hough_params* p, int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask,
+                             int32_t* d_nkept, uint64_t* d_checksum, int32_t* d_status, void* stream);
+
 /* Launch shape the library would use for these parameters: fills the zero launch fields
  * of *p (theta_tiles, events_per_cta, block) and returns HOUGH_OK or an error. */
 int hough_resolve_params(hough_params* p);

@@ -77,6 +77,7 @@ def load(build: bool = True):
                 "hough_selftest_bin": [i32, i64, i64, vp, vp],
                 "hough_probe_smem_atomics": [i32, i32, i32, i32, i32, vp, vp],
                 "hough_run_host": [vp, i64, vp, i64, P, vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp, vp],
+                "hough_run_batched_static": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -251,6 +252,19 @@ def run(xy, off, p: Params, out: Outputs | None = None, checksum: bool = False, 
     rc = fn(_ptr(xy), xy.shape[0], _ptr(off), ne, ctypes.byref(p), _ptr(out.npeaks), _ptr(out.peaks), _ptr(out.mask),
             _ptr(out.nkept), _ptr(out.checksum), _ptr(out.ws), out.ws.numel(), _ptr(out.status), _stream(stream))
     _check("hough_run_batched" if batched else "hough_run", rc)
+    return out
+
+
+def run_static(xy, off, p: Params, out: Outputs, stream=None) -> Outputs:
+    """The batched path through ``hough_run_batched_static``: no workspace from the caller, the
+    scratch comes from the library's built-in device array (``out.ws`` is not used)."""
+    torch = _torch()
+    xy = _dev(xy, "xy", torch.int32)
+    off = _dev(off, "off", torch.int64)
+    rc = load().hough_run_batched_static(
+        _ptr(xy), xy.shape[0], _ptr(off), off.shape[0] - 1, ctypes.byref(p), _ptr(out.npeaks), _ptr(out.peaks),
+        _ptr(out.mask), _ptr(out.nkept), _ptr(out.checksum), _ptr(out.status), _stream(stream))
+    _check("hough_run_batched_static", rc)
     return out
 
 

@@ -17,6 +17,9 @@ static int cuda_fail(cudaError_t e) {
   return HOUGH_ECUDA;
 }
 
+// Lets other files of the library report a CUDA error through hough_last_cuda_error.
+void note_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+
 // th_j = (j + 1/2) pi / N_theta; c_j = round(2^14 cos th_j) (half away from zero).
 void host_trig(int n_theta, TrigTable* t) {
   std::memset(t, 0, sizeof(*t));
