@@ -210,10 +210,20 @@ int hough_last_cuda_error(void);
 int hough_selftest_bin(int32_t n_rho, int64_t rho_lo, int64_t rho_hi, unsigned long long* d_mismatch,
                        void* stream);
 
+/* Checks the vote's float bin path (a float estimate of the bin, exact integer arithmetic
+ * whenever an integer lies within N_rho 2^-20 of the estimate) on n_samples pseudo-random
+ * (u_q, v_q, column) tuples of the int32 fast-path range against plain 64-bit floor
+ * division: d_out[0] (uint64, caller-zeroed) gets the disagreements, d_out[1] the number of
+ * tuples that took the exact integer path. */
+int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t n_samples, unsigned long long* d_out,
+                         void* stream);
+
 /* Shared-memory atomic ceiling: every SM runs `ctas_per_sm` CTAs of `threads` threads,
  * each thread issuing `iters` x 16 32-bit shared-memory adds into a `smem_bytes`
  * array with address pattern `mode` (0: each lane its own bank, conflict-free;
- * 1: pseudo-random words; 2: all lanes of a warp on one word). *d_sink receives a
+ * 1: pseudo-random words; 2: all lanes of a warp on one word; 3: each thread always on
+ * the same word of its own bank, so consecutive adds of a thread hit one address).
+ * *d_sink receives a
  * value that keeps the work alive. Time it with events on `stream`. */
 int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,
                              unsigned long long* d_sink, void* stream);

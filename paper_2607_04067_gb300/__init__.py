@@ -75,6 +75,7 @@ def load(build: bool = True):
                 "hough_status": [vp, vp, ctypes.POINTER(i32)],
                 "hough_last_cuda_error": [],
                 "hough_selftest_bin": [i32, i64, i64, vp, vp],
+                "hough_selftest_fpbin": [i32, i32, ctypes.c_uint64, i64, vp, vp],
                 "hough_probe_smem_atomics": [i32, i32, i32, i32, i32, vp, vp],
                 "hough_run_host": [vp, i64, vp, i64, P, vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp, vp],
                 "hough_run_batched_static": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, vp],
@@ -314,6 +315,15 @@ def selftest_bin(n_rho: int, rho_lo: int, rho_hi: int, stream=None) -> int:
     mism = torch.zeros(1, dtype=torch.int64, device="cuda")
     _check("hough_selftest_bin", load().hough_selftest_bin(n_rho, rho_lo, rho_hi, _ptr(mism), _stream(stream)))
     return mism
+
+
+def selftest_fpbin(n_theta: int, n_rho: int, seed: int, n_samples: int, stream=None):
+    """(disagreements, exact-path fallbacks) of the vote's float bin path on random tuples."""
+    torch = _torch()
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _check("hough_selftest_fpbin", load().hough_selftest_fpbin(n_theta, n_rho, seed, n_samples, _ptr(out),
+                                                               _stream(stream)))
+    return int(out[0].item()), int(out[1].item())
 
 
 def probe_smem_atomics(mode: int, ctas_per_sm: int, threads: int, smem_bytes: int, iters: int, sink, stream=None):

@@ -72,7 +72,7 @@ static int round16(int x) { return (x + 15) & ~15; }
 static bool layout(Plan& pl) {
   const int wpad = pl.groups * 32;
   const int cell = pl.acc32 ? 4 : 2;
-  const int acc_bytes = wpad * pl.nrho_pad * cell;
+  const int acc_bytes = pl.mp ? (pl.n_theta / 2) * pl.rows_phys * 4 : wpad * pl.nrho_pad * cell;
   const int sel_bytes = (2 * pl.n_theta + 64) * 4 + pl.n_theta * 8 + pl.n_theta * pl.nrb * 4;
   int o = 0;
   pl.off_acc = o;
@@ -86,6 +86,8 @@ static bool layout(Plan& pl) {
   o += round16(wpad * pl.nrb * 4);
   pl.off_cnt = o;
   o += round16(wpad * pl.scan_ranges * 4);
+  pl.off_unres = o;
+  o += round16((pl.hit_cap + 1024) / 32 * 4);
   pl.off_trig = o;
   o += round16(2 * pl.n_theta * 2);
   pl.smem_bytes = o;
@@ -117,6 +119,15 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
   pl.nrb = (p->n_rho + 31) / 32;
   pl.magic = host_magic(p->n_rho);
   pl.grab = p->events_per_cta > 0 ? p->events_per_cta : 1;
+  {
+    const double nr = p->n_rho, delta = nr * std::ldexp(1.0, -20);
+    pl.fpbin = 1;
+    pl.fp_scale = (float)(nr / (2.0 * (double)kH));
+    pl.fp_c0 = (float)(0.5 * nr);
+    pl.fp_khi = (float)(nr - 0.5);
+    pl.fp_dlo = (float)(delta - 0.5);
+    pl.fp_dhi = (float)(-delta - 0.5);
+  }
   const int cell_choice = acc32 < 0 ? 0 : acc32;
   for (int T = (p->theta_tiles ? p->theta_tiles : 1); T <= (p->theta_tiles ? p->theta_tiles : 64); ++T) {
     const int W = (p->n_theta + T - 1) / T;
@@ -129,18 +140,48 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
     const int halo = T > 1 ? 32 : 0;
     if (p->block) {
       const int work = p->block - halo;
-      if (work <= 0 || work % (pl.groups * 32)) return HOUGH_EPARAM;
+      if (work <= 0 || work % (pl.groups * 32)) {
+        if (p->theta_tiles) return HOUGH_EPARAM;
+        continue;  // this tile count cannot use the requested block; try the next
+      }
       pl.split = work / (pl.groups * 32);
     } else {
-      int s = 512 / (pl.groups * 32);
+      // as many warps as fit 1024 threads: with one CTA per SM (large accumulators) the
+      // extra warps hide the latency of the vote chains, the scan and the selection
+      int s = (1024 - halo) / (pl.groups * 32);
       if (s < 1) s = 1;
-      while (s > 1 && pl.groups * 32 * s + halo > 1024) --s;
       pl.split = s;
     }
     pl.threads = pl.groups * 32 * pl.split + halo;
     if (pl.threads > 1024) {
       if (p->theta_tiles) return HOUGH_EPARAM;
       continue;
+    }
+    // Mirror pairs need the whole theta range in one tile, whole 64-column group pairs and
+    // a table with c[N-1-j] = -c[j], s[N-1-j] = s[j] (true for round-half-away-from-zero).
+    pl.mirror = 0;
+    if (T == 1 && p->n_theta % 64 == 0) {
+      TrigTable tt;
+      host_trig(p->n_theta, &tt);
+      bool sym = true;
+      for (int j = 0; j < p->n_theta && sym; ++j)
+        sym = tt.c[p->n_theta - 1 - j] == -tt.c[j] && tt.s[p->n_theta - 1 - j] == tt.s[j];
+      pl.mirror = sym ? 1 : 0;
+    }
+    pl.mp = pl.mirror && !pl.acc32 && pl.fpbin;
+    if (pl.mp) {
+      int b = 0;
+      while ((1 << b) < p->n_rho + 2) ++b;
+      const int F = 23 - b;
+      pl.rows_phys = p->n_rho + 2;
+      pl.mp_F = F;
+      pl.mp_pmask = ((1 << b) - 1) << 7;
+      pl.mp_fmask = (1 << F) - 1;
+      pl.mp_amb_add = (int)std::ceil(p->n_rho * std::ldexp(1.0, F - 20)) + 1;
+      pl.mp_amb_lim = 2 * pl.mp_amb_add;
+      pl.mp_c0 = (float)(0.5 * p->n_rho + 1.0 + (double)(1 << b));
+      const double L = (double)kH * (1.0 + 1.0 / p->n_rho) / 16385.0;
+      pl.mp_lsq = (long long)std::floor(L * L);
     }
     int R = 4096 / (pl.groups * 32);
     if (R < 1) R = 1;
@@ -543,9 +584,20 @@ int hough_selftest_bin(int32_t n_rho, int64_t rho_lo, int64_t rho_hi, unsigned l
   return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
 }
 
+int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t n_samples, unsigned long long* d_out,
+                         void* stream) {
+  hough_params p{n_theta, n_rho, 1, 1, 1, 0, 0, 0};
+  Plan pl;
+  if (!d_out || n_samples < 0 || make_plan(&p, pl) != HOUGH_OK) return HOUGH_EINVAL;
+  TrigTable trig;
+  host_trig(n_theta, &trig);
+  cudaError_t e = launch_selftest_fpbin(pl, trig, seed, n_samples, d_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
 int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,
                              unsigned long long* d_sink, void* stream) {
-  if (!d_sink || mode < 0 || mode > 2 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads % 32) ||
+  if (!d_sink || mode < 0 || mode > 3 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads % 32) ||
       smem_bytes < 4096 || smem_bytes > kSmemBudget || iters < 1)
     return HOUGH_EINVAL;
   cudaError_t e = launch_probe_atomics(mode, ctas_per_sm, threads, smem_bytes, iters, d_sink, (cudaStream_t)stream);

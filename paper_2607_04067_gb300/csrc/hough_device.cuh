@@ -48,14 +48,13 @@ __device__ __forceinline__ int rho_bin64(long long t, BinMagic m) {
   return bin_of_t((uint32_t)t, m);
 }
 
-// floor(a / b) for b > 0. A float estimate is within one of the quotient when |a / b| < 2^20
-// (relative error below 2^-21); an exact remainder test fixes it. Larger quotients take the
-// 64-bit integer division.
-__device__ __forceinline__ long long floor_div_pos(long long a, long long b) {
-  const float q = __fdiv_rn((float)a, (float)b);
+// floor(a / b) for b > 0 given a float estimate q of a / b with relative error below
+// 2^-21: for |q| < 2^20 the estimate is within one of the quotient and an exact remainder
+// test fixes it; larger quotients take the 64-bit integer division.
+__device__ __forceinline__ long long floor_div_est(long long a, long long b, float q) {
   if (fabsf(q) < 1048576.0f) {
-    long long q0 = (long long)floorf(q);
-    const long long r = a - q0 * b;
+    int q0 = (int)floorf(q);
+    const long long r = a - (long long)q0 * b;
     if (r < 0) q0 -= 1;
     else if (r >= b) q0 += 1;
     return q0;
@@ -66,12 +65,15 @@ __device__ __forceinline__ long long floor_div_pos(long long a, long long b) {
 }
 
 // Conformal map of one hit. Returns 0, or HOUGH_F_BAD_HIT for r = 0 or a coordinate beyond 2^24 um.
+// The estimate uses x, y as floats (exact for |x|, |y| <= 2^24) and a rounded r^2.
 __device__ __forceinline__ int map_hit(int x, int y, long long& u, long long& v) {
   if (x > kCoordMax || x < -kCoordMax || y > kCoordMax || y < -kCoordMax) return HOUGH_F_BAD_HIT;
   const long long r2 = (long long)x * x + (long long)y * y;
   if (r2 == 0) return HOUGH_F_BAD_HIT;
-  u = floor_div_pos((long long)x * (1LL << 33), r2);
-  v = floor_div_pos((long long)y * (1LL << 33), r2);
+  const float fx = (float)x, fy = (float)y;
+  const float s = 8589934592.0f / fmaf(fx, fx, fy * fy);  // 2^33 / r^2
+  u = floor_div_est((long long)x * (1LL << 33), r2, fx * s);
+  v = floor_div_est((long long)y * (1LL << 33), r2, fy * s);
   return 0;
 }
 

@@ -4,12 +4,13 @@
 // Thread organisation (Sec. 3's event / angle-column / hit parallelism, redone for sm_103a):
 //   - a work item is one event, or one theta tile of an event when its accumulator
 //     does not fit one CTA's shared memory;
-//   - every lane of a "worker" warp owns one theta column of the tile for the whole
-//     vote: warp w votes column group g = w / split, hits i = p, p + split, ... with
-//     p = w % split. Lane l's cells live in shared-memory bank l only: word
-//     ((g * rows + row) * 32 + l), rows = N_rho / 2 packed int16 pairs (or N_rho
-//     int32 cells), so the column-parallel vote is free of bank conflicts whatever
-//     rho bins the hits hit, and warps sharing a column group add with red.shared;
+//   - every lane of a "worker" warp owns theta columns of the tile for the whole vote.
+//     Lane l's cells live in shared-memory bank l only: word ((g * rows + row) * 32 + l),
+//     rows = N_rho / 2 packed int16 pairs (or N_rho int32 cells), so the column-parallel
+//     vote is free of bank conflicts whatever rho bins the hits hit; warps sharing
+//     columns split the hits and add with red.shared. In mirror mode a lane owns
+//     column j and its mirror N_theta-1-j (th -> pi - th: c -> -c, s -> s), so one pair
+//     of products gives both rho values;
 //   - for tiled events one extra warp votes the two neighbour columns of the tile
 //     (halo), so the 3x3 peak test is exact on tile edges; the last tile CTA of an
 //     event (ticket counter) merges the tiles' peak lists in tile order and selects.
@@ -24,12 +25,21 @@ namespace hgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSelCap = 4;  // peak columns a lane tries alone before its hit goes to a whole warp
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
+
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t swap16(uint32_t x) { return __funnelshift_l(x, x, 16); }
 
 template <bool A32>
 __device__ __forceinline__ int acc_index(int c, int k, int nrp) {
@@ -42,12 +52,27 @@ __device__ __forceinline__ int acc_get(const uint32_t* acc, int c, int k, int nr
   return A32 ? (int)w : (int)((w >> ((k & 1) << 4)) & 0xffffu);
 }
 
+// One vote for row k of the column whose row-0 word is at shared address `colbase`.
+// No memory clobber: the accumulator is only read after a barrier, and leaving the hit
+// loads free to move above the atomics lets consecutive hits overlap.
 template <bool A32>
-__device__ __forceinline__ void vote_cell(uint32_t* colbase, int k) {
-  if (A32)
-    red_add_shared(colbase + (k << 5), 1u);
-  else
-    red_add_shared(colbase + ((k >> 1) << 5), 1u << ((k & 1) << 4));
+__device__ __forceinline__ void vote_cell(uint32_t colbase, int k) {
+  uint32_t addr, inc;
+  if (A32) {
+    addr = colbase + ((uint32_t)k << 7);
+    inc = 1u;
+  } else {
+    addr = colbase + (((uint32_t)k >> 1) << 7);
+    inc = 1u << (((uint32_t)k & 1u) << 4);
+  }
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
+}
+
+// One vote for row k of a halo column: packed int16 pairs stored contiguously.
+__device__ __forceinline__ void vote_halo(uint32_t colbase, int k) {
+  const uint32_t addr = colbase + (((uint32_t)k >> 1) << 2);
+  const uint32_t inc = 1u << (((uint32_t)k & 1u) << 4);
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
 }
 
 // In-place exclusive scan of arr[0, n) by the whole CTA; returns the total.
@@ -104,7 +129,8 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
 // Maps hits [base, base + cn) and appends those that fit the int32 fast path to hb
 // (compacted, order not kept). Valid hits beyond int32 set bit 0 of *s_flags, bad
 // hits bit 1.
-__device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn, int2* hb, int* s_nv, int* s_flags) {
+__device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn, int2* hb, int* s_nv, int* s_flags,
+                             bool as_float, long long lsq) {
   const int lane = threadIdx.x & 31;
   for (int i0 = 0; i0 < cn; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
@@ -116,13 +142,17 @@ __device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn
       st = map_hit(h.x, h.y, u, v);
       ok = (st == 0);
     }
-    const bool f = ok && fits32(u, v);
+    // fast path: int32 rho, and (mirror-pair layout) rho within one guard bin of the range
+    const bool f = ok && fits32(u, v) && (lsq == 0 || u * u + v * v <= lsq);
     const unsigned bal = __ballot_sync(kFull, f);
     if (bal) {
       int slot = 0;
       if (lane == 0) slot = atomicAdd(s_nv, __popc(bal));
       slot = __shfl_sync(kFull, slot, 0);
-      if (f) hb[slot + __popc(bal & lanemask_lt())] = make_int2((int)u, (int)v);
+      // float form for the float bin path: |u|, |v| <= 44061 are exact in float
+      if (f)
+        hb[slot + __popc(bal & lanemask_lt())] =
+            as_float ? make_int2(__float_as_int((float)u), __float_as_int((float)v)) : make_int2((int)u, (int)v);
     }
     if (ok && !f) atomicOr(s_flags, 1);
     if (st) atomicOr(s_flags, 2);
@@ -179,125 +209,567 @@ __device__ void stage_sel64(const int2* __restrict__ xy, long long base, int cn,
 
 // ---- voting ----
 
+// Which columns a worker lane owns, and where their row-0 words live.
+struct VoteLane {
+  bool on;          // lane votes
+  bool halo;        // lane of the halo warp (tiles > 1)
+  bool mirror;      // lane also votes the mirror column
+  int p, P;         // hit partition of this warp, partitions per column set
+  int cj, sj;       // trig of the (first) column
+  uint32_t col1;    // shared address of column 1, row 0
+  uint32_t col2;    // mirror column (mirror mode) or halo column
+};
+
+// Bin of the float estimate kf = u A + v B + N_rho/2 of k* = (u c + v s + H) N_rho / 2H, where
+// A = c N_rho/2H, B = s N_rho/2H in float. |kf - k*| < N_rho 2^-21 (rounding of A, B and of
+// the three float operations, each at most 2^-24 relative of a term below 1.6 N_rho), so
+// floor(kf) = floor(k*) unless an integer lies within delta = N_rho 2^-20 of kf. y1 and y2
+// round kc - 1/2 + delta and kc - 1/2 - delta to integers (adding 1.5 2^23 leaves no fraction
+// bits); they differ exactly when such an integer exists, and then the exact integer path
+// decides. Clamping kf to [1/2, N_rho - 1/2] first gives the edge bins for rho outside the
+// range, as the integer clamp does.
+struct FpBin {
+  float khi, dlo, dhi;
+};
+
+__device__ __forceinline__ int bin_fp(float kf, const FpBin& K, float uf, float vf, int c, int s, BinMagic m) {
+  const float kc = fminf(fmaxf(kf, 0.5f), K.khi);
+  const float y1 = __fadd_rn(__fadd_rn(kc, K.dlo), 12582912.0f);
+  const float y2 = __fadd_rn(__fadd_rn(kc, K.dhi), 12582912.0f);
+  int r = __float_as_int(y1) - 0x4B400000;
+  if (__float_as_int(y1) != __float_as_int(y2)) {
+    const int u = __float2int_rn(uf), v = __float2int_rn(vf);
+    r = rho_bin32(u * c + (v * s + (int)kH), m);
+  }
+  return r;
+}
+
 template <bool A32>
-__device__ __forceinline__ void vote32(const Plan& pl, uint32_t* acc, int* halo, const int2* hb, int nv, int cj,
-                                       int sj, bool col_ok, bool halo_warp, int hc, int hs, int g, int p,
-                                       int lane) {
+__device__ __forceinline__ void vote32_fp(const Plan& pl, const VoteLane& L, const int2* hb, int nv) {
+  if (!L.on) return;
+  const BinMagic m = pl.magic;
+  const FpBin K{pl.fp_khi, pl.fp_dlo, pl.fp_dhi};
+  const float c0 = pl.fp_c0;
+  const int cj = L.cj, sj = L.sj;
+  const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
+  if (L.halo) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane & 15; i < nv; i += 16) {
+      const float2 h = reinterpret_cast<const float2*>(hb)[i];
+      vote_halo(L.col2, bin_fp(__fmaf_rn(h.x, A, __fmaf_rn(h.y, B, c0)), K, h.x, h.y, cj, sj, m));
+    }
+    return;
+  }
+  const float4* hb4 = reinterpret_cast<const float4*>(hb);
+  const int np = nv >> 1, P = L.P;
+  if (L.mirror) {
+#pragma unroll 2
+    for (int q = L.p; q < np; q += P) {
+      const float4 h = hb4[q];
+      const float v0 = __fmaf_rn(h.y, B, c0), v1 = __fmaf_rn(h.w, B, c0);
+      vote_cell<A32>(L.col1, bin_fp(__fmaf_rn(h.x, A, v0), K, h.x, h.y, cj, sj, m));
+      vote_cell<A32>(L.col2, bin_fp(__fmaf_rn(-h.x, A, v0), K, h.x, h.y, -cj, sj, m));
+      vote_cell<A32>(L.col1, bin_fp(__fmaf_rn(h.z, A, v1), K, h.z, h.w, cj, sj, m));
+      vote_cell<A32>(L.col2, bin_fp(__fmaf_rn(-h.z, A, v1), K, h.z, h.w, -cj, sj, m));
+    }
+    if ((nv & 1) && L.p == np % P) {
+      const float2 h = reinterpret_cast<const float2*>(hb)[nv - 1];
+      const float v0 = __fmaf_rn(h.y, B, c0);
+      vote_cell<A32>(L.col1, bin_fp(__fmaf_rn(h.x, A, v0), K, h.x, h.y, cj, sj, m));
+      vote_cell<A32>(L.col2, bin_fp(__fmaf_rn(-h.x, A, v0), K, h.x, h.y, -cj, sj, m));
+    }
+  } else {
+#pragma unroll 4
+    for (int q = L.p; q < np; q += P) {
+      const float4 h = hb4[q];
+      vote_cell<A32>(L.col1, bin_fp(__fmaf_rn(h.x, A, __fmaf_rn(h.y, B, c0)), K, h.x, h.y, cj, sj, m));
+      vote_cell<A32>(L.col1, bin_fp(__fmaf_rn(h.z, A, __fmaf_rn(h.w, B, c0)), K, h.z, h.w, cj, sj, m));
+    }
+    if ((nv & 1) && L.p == np % P) {
+      const float2 h = reinterpret_cast<const float2*>(hb)[nv - 1];
+      vote_cell<A32>(L.col1, bin_fp(__fmaf_rn(h.x, A, __fmaf_rn(h.y, B, c0)), K, h.x, h.y, cj, sj, m));
+    }
+  }
+}
+
+template <bool A32>
+__device__ __forceinline__ void vote32(const Plan& pl, const VoteLane& L, const int2* hb, int nv) {
+  if (!L.on) return;
   const int Hh = (int)kH;
   const BinMagic m = pl.magic;
-  if (!halo_warp) {
-    if (!col_ok) return;
-    uint32_t* colbase = acc + ((A32 ? g * pl.nrho_pad : g * (pl.nrho_pad >> 1)) << 5) + lane;
-    const int4* hb4 = reinterpret_cast<const int4*>(hb);
-    const int np = nv >> 1, P = pl.split;
-#pragma unroll 4
-    for (int q = p; q < np; q += P) {
-      const int4 h = hb4[q];
-      const int k0 = rho_bin32(h.x * cj + (h.y * sj + Hh), m);
-      const int k1 = rho_bin32(h.z * cj + (h.w * sj + Hh), m);
-      vote_cell<A32>(colbase, k0);
-      vote_cell<A32>(colbase, k1);
-    }
-    if ((nv & 1) && p == np % P) {
-      const int2 h = hb[nv - 1];
-      vote_cell<A32>(colbase, rho_bin32(h.x * cj + (h.y * sj + Hh), m));
-    }
-  } else {
-    int* hcol = halo + (lane >> 4) * pl.nrho_pad;
+  const int cj = L.cj, sj = L.sj;
+  if (L.halo) {
+    const int lane = threadIdx.x & 31;
     for (int i = lane & 15; i < nv; i += 16) {
       const int2 h = hb[i];
-      red_add_shared(reinterpret_cast<uint32_t*>(hcol + rho_bin32(h.x * hc + (h.y * hs + Hh), m)), 1u);
+      vote_halo(L.col2, rho_bin32(h.x * cj + (h.y * sj + Hh), m));
+    }
+    return;
+  }
+  const int4* hb4 = reinterpret_cast<const int4*>(hb);
+  const int np = nv >> 1, P = L.P;
+  if (L.mirror) {
+#pragma unroll 2
+    for (int q = L.p; q < np; q += P) {
+      const int4 h = hb4[q];
+      const int v0 = h.y * sj + Hh, u0 = h.x * cj;
+      const int v1 = h.w * sj + Hh, u1 = h.z * cj;
+      vote_cell<A32>(L.col1, rho_bin32(v0 + u0, m));
+      vote_cell<A32>(L.col2, rho_bin32(v0 - u0, m));
+      vote_cell<A32>(L.col1, rho_bin32(v1 + u1, m));
+      vote_cell<A32>(L.col2, rho_bin32(v1 - u1, m));
+    }
+    if ((nv & 1) && L.p == np % P) {
+      const int2 h = hb[nv - 1];
+      const int v0 = h.y * sj + Hh, u0 = h.x * cj;
+      vote_cell<A32>(L.col1, rho_bin32(v0 + u0, m));
+      vote_cell<A32>(L.col2, rho_bin32(v0 - u0, m));
+    }
+  } else {
+#pragma unroll 4
+    for (int q = L.p; q < np; q += P) {
+      const int4 h = hb4[q];
+      vote_cell<A32>(L.col1, rho_bin32(h.x * cj + (h.y * sj + Hh), m));
+      vote_cell<A32>(L.col1, rho_bin32(h.z * cj + (h.w * sj + Hh), m));
+    }
+    if ((nv & 1) && L.p == np % P) {
+      const int2 h = hb[nv - 1];
+      vote_cell<A32>(L.col1, rho_bin32(h.x * cj + (h.y * sj + Hh), m));
     }
   }
 }
 
 template <bool A32>
-__device__ __forceinline__ void vote64(const Plan& pl, uint32_t* acc, int* halo, const longlong2* hw, int nv, int cj,
-                                       int sj, bool col_ok, bool halo_warp, int hc, int hs, int g, int p,
-                                       int lane) {
+__device__ __forceinline__ void vote64(const Plan& pl, const VoteLane& L, const longlong2* hw, int nv) {
+  if (!L.on) return;
   const BinMagic m = pl.magic;
-  if (!halo_warp) {
-    if (!col_ok) return;
-    uint32_t* colbase = acc + ((A32 ? g * pl.nrho_pad : g * (pl.nrho_pad >> 1)) << 5) + lane;
-    for (int q = p; q < nv; q += pl.split) {
-      const longlong2 h = hw[q];
-      vote_cell<A32>(colbase, rho_bin64(h.x * cj + h.y * sj + kH, m));
-    }
-  } else {
-    int* hcol = halo + (lane >> 4) * pl.nrho_pad;
+  const long long cj = L.cj, sj = L.sj;
+  if (L.halo) {
+    const int lane = threadIdx.x & 31;
     for (int i = lane & 15; i < nv; i += 16) {
       const longlong2 h = hw[i];
-      red_add_shared(reinterpret_cast<uint32_t*>(hcol + rho_bin64(h.x * hc + h.y * hs + kH, m)), 1u);
+      vote_halo(L.col2, rho_bin64(h.x * cj + h.y * sj + kH, m));
+    }
+    return;
+  }
+  for (int q = L.p; q < nv; q += L.P) {
+    const longlong2 h = hw[q];
+    const long long vs = h.y * sj + kH, uc = h.x * cj;
+    vote_cell<A32>(L.col1, rho_bin64(vs + uc, m));
+    if (L.mirror) vote_cell<A32>(L.col2, rho_bin64(vs - uc, m));
+  }
+}
+
+// ---- mirror-pair word layout (untiled events, N_theta a multiple of 64) ----
+// Word lane w in [0, N_theta/2) holds column w in its low half and column N_theta-1-w (its
+// mirror) in its high half, one word per physical row p = k + 1. Rows p = 0 and p = N_rho + 1
+// are guard rows: the fast path only takes hits whose rho stays within half a bin of the range,
+// so its unclamped bins fall in [-1, N_rho]; the guard rows are folded into rows 0 and
+// N_rho - 1 after the vote, which is what clamping would have done.
+
+__device__ __forceinline__ int mp_word(int w, int p, int rows_phys) {
+  return (((w >> 5) * rows_phys + p) << 5) + (w & 31);
+}
+
+__device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, const Plan& pl) {
+  const int NT = pl.n_theta;
+  const bool hi = c >= (NT >> 1);
+  const uint32_t x = acc[mp_word(hi ? NT - 1 - c : c, k + 1, pl.rows_phys)];
+  return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
+}
+
+// Byte offset of the row of the vote whose float estimate, shifted by 1 + 2^b (2^b > N_rho + 1),
+// is kfp. In [2^b, 2^(b+1)) a float's low F = 23 - b bits are the fraction and the bits above
+// them the integer part, so both come straight from the bit pattern. The estimate is within
+// N_rho 2^-21 + 2^-(F+1) of the exact value; if the fraction is within amb_add / 2^F of an
+// integer the exact integer path (clamped) decides.
+__device__ __forceinline__ uint32_t mp_row_off(float kfp, const Plan& pl, float uf, float vf, int c, int s) {
+  const uint32_t y = (uint32_t)__float_as_int(kfp);
+  if (((y + (uint32_t)pl.mp_amb_add) & (uint32_t)pl.mp_fmask) < (uint32_t)pl.mp_amb_lim) {
+    const int u = __float2int_rn(uf), v = __float2int_rn(vf);
+    return (uint32_t)(rho_bin32(u * c + (v * s + (int)kH), pl.magic) + 1) << 7;
+  }
+  return (y >> (pl.mp_F - 7)) & (uint32_t)pl.mp_pmask;
+}
+
+__device__ __forceinline__ void red_u32(uint32_t addr, uint32_t inc) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
+}
+
+__device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, const int2* hb, int nv) {
+  const int cj = L.cj, sj = L.sj;
+  const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
+  const float c0 = pl.mp_c0;
+  const uint32_t base = L.col1;
+  const float4* hb4 = reinterpret_cast<const float4*>(hb);
+  const int np = nv >> 1, P = L.P;
+#pragma unroll 2
+  for (int q = L.p; q < np; q += P) {
+    const float4 h = hb4[q];
+    const float v0 = __fmaf_rn(h.y, B, c0), v1 = __fmaf_rn(h.w, B, c0);
+    red_u32(base + mp_row_off(__fmaf_rn(h.x, A, v0), pl, h.x, h.y, cj, sj), 1u);
+    red_u32(base + mp_row_off(__fmaf_rn(-h.x, A, v0), pl, h.x, h.y, -cj, sj), 0x10000u);
+    red_u32(base + mp_row_off(__fmaf_rn(h.z, A, v1), pl, h.z, h.w, cj, sj), 1u);
+    red_u32(base + mp_row_off(__fmaf_rn(-h.z, A, v1), pl, h.z, h.w, -cj, sj), 0x10000u);
+  }
+  if ((nv & 1) && L.p == np % P) {
+    const float2 h = reinterpret_cast<const float2*>(hb)[nv - 1];
+    const float v0 = __fmaf_rn(h.y, B, c0);
+    red_u32(base + mp_row_off(__fmaf_rn(h.x, A, v0), pl, h.x, h.y, cj, sj), 1u);
+    red_u32(base + mp_row_off(__fmaf_rn(-h.x, A, v0), pl, h.x, h.y, -cj, sj), 0x10000u);
+  }
+}
+
+__device__ __forceinline__ void vote_mp64(const Plan& pl, const VoteLane& L, const longlong2* hw, int nv) {
+  const BinMagic m = pl.magic;
+  const long long cj = L.cj, sj = L.sj;
+  for (int q = L.p; q < nv; q += L.P) {
+    const longlong2 h = hw[q];
+    const long long vs = h.y * sj + kH, uc = h.x * cj;
+    red_u32(L.col1 + ((uint32_t)(rho_bin64(vs + uc, m) + 1) << 7), 1u);
+    red_u32(L.col1 + ((uint32_t)(rho_bin64(vs - uc, m) + 1) << 7), 0x10000u);
+  }
+}
+
+// Guard rows into the edge rows (both halves at once: a column holds at most 32767 votes,
+// so the packed add never carries across halves).
+__device__ void mp_fold(const Plan& pl, uint32_t* acc) {
+  const int rp = pl.rows_phys, NR = pl.n_rho;
+  for (int w = threadIdx.x; w < (pl.n_theta >> 1); w += blockDim.x) {
+    uint32_t* col = acc + mp_word(w, 0, rp);
+    col[32] += col[0];
+    col[NR << 5] += col[(NR + 1) << 5];
+  }
+}
+
+// Peak scan of the mirror-pair layout: one row per step, both columns of a word at once.
+// For word lane w, lane w-1 holds the left neighbour of column w and the right neighbour of
+// column N-1-w; lane w+1 the other two. Lane w = -1 supplies the theta wrap (word lane 0, rows
+// mirrored, halves swapped) and lane w = N/2 the middle (word lane N/2-1, halves swapped).
+__device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, int* cnt, bool do_cs,
+                        unsigned long long& csum) {
+  const int NT = pl.n_theta, NR = pl.n_rho, R = pl.scan_ranges, half = NT >> 1, rp = pl.rows_phys;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nblk = (half + 29) / 30;
+  const uint32_t TT = (uint32_t)pl.threshold | ((uint32_t)pl.threshold << 16);
+  for (int u = warp; u < nblk * R; u += nwarps) {
+    const int b = u / R, r = u % R;
+    const int k0 = (NR * r) / R, k1 = (NR * (r + 1)) / R;
+    const int w = b * 30 + lane - 1;
+    int sw = w;
+    bool mir = false, swp = false, none = false;
+    if (w < 0) {
+      sw = 0;
+      mir = true;
+      swp = true;
+    } else if (w >= half) {
+      if (w == half) {
+        sw = half - 1;
+        swp = true;
+      } else {
+        none = true;
+        sw = 0;
+      }
+    }
+    const uint32_t* col = acc + mp_word(sw, 1, rp);  // physical row 1 = logical row 0
+    auto fetch = [&](int k) -> uint32_t {
+      if (none || k < 0 || k >= NR) return 0u;
+      const uint32_t x = col[(mir ? NR - 1 - k : k) << 5];
+      return swp ? swap16(x) : x;
+    };
+    const bool tested = lane >= 1 && lane <= 30 && w >= 0 && w < half;
+    const bool lo_lstrict = (w != 0), hi_rstrict = (w == 0);
+    const int clo = w, chi = NT - 1 - w;
+    uint32_t U = fetch(k0 - 1), C = fetch(k0);
+    int n_lo = 0, n_hi = 0;
+    for (int k = k0; k < k1; ++k) {
+      const uint32_t D = fetch(k + 1);
+      const uint32_t VM = vmax2(vmax2(U, C), D);
+      const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
+      const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
+      if (tested) {
+        const uint32_t X = vmax2(vmax2(vmax2(U, D), vmax2(VU, VD)), TT);
+        const uint32_t Y = vmax2(X, C) ^ C;  // half is 0 where C >= every neighbour and T
+        if ((Y & 0xffffu) == 0u) {
+          const int a = C & 0xffff;
+          if (a > (int)(U & 0xffff) && (!lo_lstrict || a > (int)(VU & 0xffff))) {
+            atomicOr(&pbits[clo * pl.nrb + (k >> 5)], 1u << (k & 31));
+            ++n_lo;
+          }
+        }
+        if ((Y >> 16) == 0u) {
+          const int a = C >> 16;
+          if (a > (int)(U >> 16) && a > (int)(VD >> 16) && (!hi_rstrict || a > (int)(VU >> 16))) {
+            atomicOr(&pbits[chi * pl.nrb + (k >> 5)], 1u << (k & 31));
+            ++n_hi;
+          }
+        }
+        if (do_cs) {
+          const unsigned a0 = C & 0xffffu, a1 = C >> 16;
+          if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)clo * NR + k + 1);
+          if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)chi * NR + k + 1);
+        }
+      }
+      U = C;
+      C = D;
+    }
+    if (tested) {
+      cnt[clo * R + r] = n_lo;
+      cnt[chi * R + r] = n_hi;
     }
   }
 }
 
-// ---- selection: one lane per hit, pulling hits dynamically, testing peak columns in
-// decreasing order of peak count until one accepts the hit ----
+// ---- peak scan ----
+
+// Row range [k0, k1) of scan range r (word aligned in the packed scan).
+__device__ __forceinline__ void scan_rows(const Plan& pl, bool packed, int r, int& k0, int& k1) {
+  const int R = pl.scan_ranges;
+  if (packed) {
+    const int W2 = pl.n_rho >> 1;
+    k0 = 2 * ((W2 * r) / R);
+    k1 = 2 * ((W2 * (r + 1)) / R);
+  } else {
+    k0 = (pl.n_rho * r) / R;
+    k1 = (pl.n_rho * (r + 1)) / R;
+  }
+}
+
+// Column source of one scan lane: the tile column itself, a halo column, or the tile's own
+// far column mirrored (theta wrap of an untiled event), or nothing.
+struct ScanSrc {
+  int kind;  // 0 tile column, 1 left halo, 2 right halo, 3 none
+  int col;   // tile column for kind 0
+  bool mir;  // rows mirrored (k -> N_rho - 1 - k)
+};
+
+__device__ __forceinline__ ScanSrc scan_src(int c, int wt, int T, int j0, int NT) {
+  ScanSrc s{0, c, false};
+  if (c < 0) {
+    if (T == 1) {
+      s.col = wt - 1;
+      s.mir = true;
+    } else {
+      s.kind = 1;
+      s.mir = (j0 == 0);
+    }
+  } else if (c >= wt) {
+    if (c == wt) {
+      if (T == 1) {
+        s.col = 0;
+        s.mir = true;
+      } else {
+        s.kind = 2;
+        s.mir = (j0 + wt == NT);
+      }
+    } else {
+      s.kind = 3;
+    }
+  }
+  return s;
+}
+
+// Packed int16 scan (N_rho even): two rows per step, max.u16x2 for the 3-row column maxima,
+// one shuffle each way for the neighbour columns, exact tie test only for candidates.
+// Missing neighbours (rho edges, no column) read as 0, which never blocks a cell >= T >= 1.
+__device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t* halo, uint32_t* pbits, int* cnt,
+                            int wt, int T, int j0, bool do_cs, unsigned long long& csum) {
+  const int NT = pl.n_theta, NR = pl.n_rho, W2 = NR >> 1, R = pl.scan_ranges;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nblk = (wt + 29) / 30;
+  const uint32_t TT = (uint32_t)pl.threshold | ((uint32_t)pl.threshold << 16);
+  for (int u = warp; u < nblk * R; u += nwarps) {
+    const int b = u / R, r = u % R;
+    int k0, k1;
+    scan_rows(pl, true, r, k0, k1);
+    const int w0 = k0 >> 1, w1 = k1 >> 1;
+    const int c = b * 30 + lane - 1;
+    const ScanSrc s = scan_src(c, wt, T, j0, NT);
+    const uint32_t* col = nullptr;
+    int stride = 32;
+    if (s.kind == 0) {
+      col = acc + ((s.col >> 5) * W2 << 5) + (s.col & 31);
+    } else if (s.kind < 3) {
+      col = halo + (s.kind - 1) * W2;
+      stride = 1;
+    }
+    auto fetch = [&](int w) -> uint32_t {
+      if (!col || w < 0 || w >= W2) return 0u;
+      const uint32_t x = col[(s.mir ? W2 - 1 - w : w) * stride];
+      return s.mir ? swap16(x) : x;
+    };
+    const bool tested = lane >= 1 && lane <= 30 && c >= 0 && c < wt;
+    const bool lstrict = !(c == 0 && j0 == 0);
+    const bool rstrict = (c == wt - 1) && (j0 + wt == NT);
+    uint32_t P = fetch(w0 - 1), C = fetch(w0);
+    int cnt_l = 0;
+    const unsigned long long cell0 = (unsigned long long)(j0 + c) * NR;
+    for (int w = w0; w < w1; ++w) {
+      const uint32_t N = fetch(w + 1);
+      const uint32_t U = __funnelshift_r(P, C, 16);   // rows 2w-1, 2w
+      const uint32_t D = __funnelshift_r(C, N, 16);   // rows 2w+1, 2w+2
+      const uint32_t VM = vmax2(vmax2(U, C), D);
+      const uint32_t VL = __shfl_up_sync(kFull, VM, 1);
+      const uint32_t VR = __shfl_down_sync(kFull, VM, 1);
+      if (tested) {
+        const uint32_t X = vmax2(vmax2(vmax2(U, D), vmax2(VL, VR)), TT);
+        const uint32_t Y = vmax2(X, C) ^ C;  // half is 0 where C >= every neighbour and T
+        if ((Y & 0xffffu) == 0u || (Y >> 16) == 0u) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int sh = hh << 4;
+            if ((Y >> sh) & 0xffffu) continue;
+            const int av = (C >> sh) & 0xffff, up = (U >> sh) & 0xffff;
+            const int lv = (VL >> sh) & 0xffff, rv = (VR >> sh) & 0xffff;
+            if (av > up && (!lstrict || av > lv) && (!rstrict || av > rv)) {
+              const int k = 2 * w + hh;
+              atomicOr(&pbits[c * pl.nrb + (k >> 5)], 1u << (k & 31));
+              ++cnt_l;
+            }
+          }
+        }
+        if (do_cs) {
+          const unsigned a0 = C & 0xffffu, a1 = C >> 16;
+          if (a0) csum += (unsigned long long)a0 * mix64(cell0 + 2 * w + 1);
+          if (a1) csum += (unsigned long long)a1 * mix64(cell0 + 2 * w + 2);
+        }
+      }
+      P = C;
+      C = N;
+    }
+    if (tested) cnt[c * R + r] = cnt_l;
+  }
+}
+
+// Scalar scan for the int32-cell layout or an odd N_rho: one row per step.
+template <bool A32>
+__device__ void scan_scalar(const Plan& pl, const uint32_t* acc, const uint32_t* halo, uint32_t* pbits, int* cnt,
+                            int wt, int T, int j0, bool do_cs, unsigned long long& csum) {
+  const int NT = pl.n_theta, NR = pl.n_rho, nrp = pl.nrho_pad, R = pl.scan_ranges;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nblk = (wt + 29) / 30;
+  for (int u = warp; u < nblk * R; u += nwarps) {
+    const int b = u / R, r = u % R;
+    int k0, k1;
+    scan_rows(pl, false, r, k0, k1);
+    const int c = b * 30 + lane - 1;
+    const ScanSrc s = scan_src(c, wt, T, j0, NT);
+    auto fetch = [&](int kk) -> int {
+      const int rr = s.mir ? NR - 1 - kk : kk;
+      if (s.kind == 3 || rr < 0 || rr >= NR) return -1;
+      if (s.kind == 0) return acc_get<A32>(acc, s.col, rr, nrp);
+      return (int)((halo[(s.kind - 1) * (nrp >> 1) + (rr >> 1)] >> ((rr & 1) << 4)) & 0xffffu);
+    };
+    const bool tested = lane >= 1 && lane <= 30 && c >= 0 && c < wt;
+    const bool lstrict = !(c == 0 && j0 == 0);
+    const bool rstrict = (c == wt - 1) && (j0 + wt == NT);
+    int vp = fetch(k0 - 1), vc = fetch(k0);
+    int cnt_l = 0;
+    const unsigned long long cell0 = (unsigned long long)(j0 + c) * NR;
+    for (int k = k0; k < k1; ++k) {
+      const int vn = fetch(k + 1);
+      const int vm = max(max(vp, vc), vn);
+      const int vmL = __shfl_up_sync(kFull, vm, 1);
+      const int vmR = __shfl_down_sync(kFull, vm, 1);
+      if (tested && vc >= pl.threshold && vc > vp && vc >= vn && (lstrict ? vc > vmL : vc >= vmL) &&
+          (rstrict ? vc > vmR : vc >= vmR)) {
+        atomicOr(&pbits[c * pl.nrb + (k >> 5)], 1u << (k & 31));
+        ++cnt_l;
+      }
+      if (do_cs && tested && vc > 0) csum += (unsigned long long)vc * mix64(cell0 + k + 1);
+      vp = vc;
+      vc = vn;
+    }
+    if (tested) cnt[c * R + r] = cnt_l;
+  }
+}
+
+// ---- selection: a lane tries the kSelCap most populated peak columns for its hit; hits
+// still open go to a whole warp that tests 32 columns per step ----
 
 template <bool WIDE>
-__device__ int select_pull(const Plan& pl, const void* buf, int cn, long long mbase, uint8_t* __restrict__ mask,
-                           const int2* cs, const uint32_t* bm, int D, int* s_next) {
-  const int lane = threadIdx.x & 31;
-  const BinMagic m = pl.magic;
+__device__ __forceinline__ bool sel_test(const Plan& pl, long long u, long long v, int2 c2, const uint32_t* bmd) {
+  const int k = WIDE ? rho_bin64(u * c2.x + v * c2.y + kH, pl.magic)
+                     : rho_bin32((int)u * c2.x + ((int)v * c2.y + (int)kH), pl.magic);
+  return (bmd[k >> 5] >> (k & 31)) & 1u;
+}
+
+template <bool WIDE>
+__device__ int select_chunk(const Plan& pl, const void* buf, int cn, long long mbase, uint8_t* __restrict__ mask,
+                            const int2* cs, const uint32_t* bm, int D, uint32_t* unres) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nrb = pl.nrb;
-  int i = -1, d = 0, kept = 0;
-  bool fin = false;
-  long long u = 0, v = 0;
-  for (;;) {
-    const bool need = (i < 0) && !fin;
-    const unsigned nb = __ballot_sync(kFull, need);
-    if (nb) {
-      const int leader = __ffs(nb) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(s_next, __popc(nb));
-      base = __shfl_sync(kFull, base, leader);
-      if (need) {
-        const int ii = base + __popc(nb & lanemask_lt());
-        if (ii < cn) {
-          bool bad;
-          if (WIDE) {
-            const longlong2 h = reinterpret_cast<const longlong2*>(buf)[ii];
-            u = h.x;
-            v = h.y;
-            bad = (h.x == LLONG_MIN);
-          } else {
-            const int2 h = reinterpret_cast<const int2*>(buf)[ii];
-            u = h.x;
-            v = h.y;
-            bad = (h.x == INT_MIN);
-          }
-          if (bad)
-            mask[mbase + ii] = 0;
-          else {
-            i = ii;
-            d = 0;
-          }
+  const int cap = min(D, kSelCap);
+  int kept = 0;
+  for (int i0 = 0; i0 < cn; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    bool hard = false;
+    if (i < cn) {
+      long long u, v;
+      bool bad;
+      if (WIDE) {
+        const longlong2 h = reinterpret_cast<const longlong2*>(buf)[i];
+        u = h.x;
+        v = h.y;
+        bad = (h.x == LLONG_MIN);
+      } else {
+        const int2 h = reinterpret_cast<const int2*>(buf)[i];
+        u = h.x;
+        v = h.y;
+        bad = (h.x == INT_MIN);
+      }
+      bool m = false;
+      if (!bad)
+        for (int d = 0; d < cap && !m; ++d) m = sel_test<WIDE>(pl, u, v, cs[d], bm + d * nrb);
+      if (m) {
+        mask[mbase + i] = 1;
+        ++kept;
+      } else if (bad || cap == D) {
+        mask[mbase + i] = 0;
+      } else {
+        hard = true;
+      }
+    }
+    const unsigned hb = __ballot_sync(kFull, hard);
+    if (lane == 0) unres[(i0 >> 5) + warp] = hb;
+  }
+  __syncthreads();
+  if (D > cap) {
+    const int nw = (cn + 31) >> 5;
+    for (int wi = warp; wi < nw; wi += nwarps) {
+      uint32_t bits = unres[wi];
+      while (bits) {
+        const int i = (wi << 5) + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        long long u, v;
+        if (WIDE) {
+          const longlong2 h = reinterpret_cast<const longlong2*>(buf)[i];
+          u = h.x;
+          v = h.y;
         } else {
-          fin = true;
+          const int2 h = reinterpret_cast<const int2*>(buf)[i];
+          u = h.x;
+          v = h.y;
+        }
+        bool m = false;
+        for (int d0 = cap; d0 < D && !m; d0 += 32) {
+          const int d = d0 + lane;
+          const bool t = d < D && sel_test<WIDE>(pl, u, v, cs[d], bm + d * nrb);
+          m = __any_sync(kFull, t);
+        }
+        if (lane == 0) {
+          mask[mbase + i] = m ? 1 : 0;
+          kept += m;
         }
       }
     }
-    if (__all_sync(kFull, fin)) break;
-    if (i >= 0) {
-      const int2 c2 = cs[d];
-      const int k = WIDE ? rho_bin64(u * c2.x + v * c2.y + kH, m)
-                         : rho_bin32((int)u * c2.x + ((int)v * c2.y + (int)kH), m);
-      if ((bm[d * nrb + (k >> 5)] >> (k & 31)) & 1u) {
-        mask[mbase + i] = 1;
-        ++kept;
-        i = -1;
-      } else if (++d == D) {
-        mask[mbase + i] = 0;
-        i = -1;
-      }
-    }
   }
+  __syncthreads();
   return kept;
 }
 
 struct ItemShared {
-  int nv, flags, wide, next, last, total, D;
+  int nv, flags, wide, last, total, D;
   int kept_tot;
   long long tstart[64];
   int tmp[32];
@@ -313,6 +785,7 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   int* hist = colidx + NT;
   int2* cs = reinterpret_cast<int2*>(hist + 64);
   uint32_t* bm = reinterpret_cast<uint32_t*>(cs + NT);
+  uint32_t* unres = reinterpret_cast<uint32_t*>(smem + pl.off_unres);
   for (int i = tid; i < NT; i += bd) colcnt[i] = 0;
   for (int i = tid; i < 64; i += bd) hist[i] = 0;
   __syncthreads();
@@ -368,27 +841,21 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   longlong2* hw64 = reinterpret_cast<longlong2*>(smem + pl.off_hits);
   for (int h0 = 0; h0 < n; h0 += pl.hit_cap) {
     const int cn = min(pl.hit_cap, n - h0);
-    if (tid == 0) {
-      sh.wide = 0;
-      sh.next = 0;
-    }
+    if (tid == 0) sh.wide = 0;
     __syncthreads();
     stage_sel32(io.xy, a + h0, cn, hb, &sh.wide);
     __syncthreads();
     if (!sh.wide) {
-      kept += select_pull<false>(pl, hb, cn, a + h0, io.mask, cs, bm, D, &sh.next);
+      kept += select_chunk<false>(pl, hb, cn, a + h0, io.mask, cs, bm, D, unres);
     } else {
       const int half = pl.hit_cap >> 1;
       for (int s0 = 0; s0 < cn; s0 += half) {
         const int sn = min(half, cn - s0);
-        __syncthreads();
-        if (tid == 0) sh.next = 0;
         stage_sel64(io.xy, a + h0 + s0, sn, hw64);
         __syncthreads();
-        kept += select_pull<true>(pl, hw64, sn, a + h0 + s0, io.mask, cs, bm, D, &sh.next);
+        kept += select_chunk<true>(pl, hw64, sn, a + h0 + s0, io.mask, cs, bm, D, unres);
       }
     }
-    __syncthreads();
   }
   return kept;
 }
@@ -397,7 +864,7 @@ template <bool A32>
 __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh, long long item,
                          bool do_cs) {
   uint32_t* acc = reinterpret_cast<uint32_t*>(smem + pl.off_acc);
-  int* halo = reinterpret_cast<int*>(smem + pl.off_halo);
+  uint32_t* halo = reinterpret_cast<uint32_t*>(smem + pl.off_halo);
   int2* hb = reinterpret_cast<int2*>(smem + pl.off_hits);
   longlong2* hw = reinterpret_cast<longlong2*>(smem + pl.off_hits);
   uint32_t* pbits = reinterpret_cast<uint32_t*>(smem + pl.off_pbits);
@@ -415,24 +882,53 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   const int j0 = t * pl.tile_w;
   const int wt = min(pl.tile_w, NT - j0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x;
-  const int nwork = pl.groups * pl.split;
-  const bool halo_warp = (warp >= nwork);
-  const int g = warp / pl.split, p = warp % pl.split;
-  const int cl = g * 32 + lane;
-  const bool col_ok = !halo_warp && cl < wt;
-  const int hl = (j0 - 1 + NT) % NT, hr = (j0 + wt) % NT;
-  int cj = 0, sj = 0, hc = 0, hs = 0;
-  if (col_ok) {
-    cj = tc[j0 + cl];
-    sj = ts[j0 + cl];
-  }
-  if (halo_warp) {
-    const int jh = lane < 16 ? hl : hr;
-    hc = tc[jh];
-    hs = ts[jh];
-  }
   const int R = pl.scan_ranges;
   const int wpad = pl.groups * 32;
+  const int rows_w = A32 ? nrp : (nrp >> 1);  // words per column
+
+  // lane roles of the vote
+  VoteLane L;
+  L.mirror = pl.mirror != 0;
+  L.halo = warp >= pl.groups * pl.split;
+  L.on = false;
+  L.cj = L.sj = 0;
+  L.col1 = L.col2 = 0;
+  const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  if (L.halo) {
+    const int jh = lane < 16 ? (j0 - 1 + NT) % NT : (j0 + wt) % NT;
+    L.on = true;
+    L.cj = tc[jh];
+    L.sj = ts[jh];
+    L.col2 = (uint32_t)__cvta_generic_to_shared(halo) + (uint32_t)((lane >> 4) * (nrp >> 1)) * 4u;
+    L.p = 0;
+    L.P = 1;
+  } else if (L.mirror) {
+    const int P2 = 2 * pl.split;
+    const int gpair = warp / P2, g2 = pl.groups - 1 - gpair;
+    L.p = warp % P2;
+    L.P = P2;
+    const int c1 = gpair * 32 + lane;
+    L.on = true;
+    L.cj = tc[j0 + c1];
+    L.sj = ts[j0 + c1];
+    if (pl.mp) {
+      L.col1 = acc_s + (uint32_t)mp_word(c1, 0, pl.rows_phys) * 4u;
+    } else {
+      L.col1 = acc_s + (uint32_t)(((gpair * rows_w) << 5) + lane) * 4u;
+      L.col2 = acc_s + (uint32_t)(((g2 * rows_w) << 5) + (31 - lane)) * 4u;
+    }
+  } else {
+    const int g = warp / pl.split;
+    L.p = warp % pl.split;
+    L.P = pl.split;
+    const int c1 = g * 32 + lane;
+    L.on = c1 < wt;
+    if (L.on) {
+      L.cj = tc[j0 + c1];
+      L.sj = ts[j0 + c1];
+    }
+    L.col1 = acc_s + (uint32_t)(((g * rows_w) << 5) + lane) * 4u;
+  }
 
   // 1. clear accumulator, halo columns, peak bitmap and counters
   __syncthreads();
@@ -441,7 +937,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     const int nz = pl.region_bytes >> 4;
     for (int i = tid; i < nz; i += bd) z[i] = make_uint4(0u, 0u, 0u, 0u);
     if (T > 1)
-      for (int i = tid; i < 2 * nrp; i += bd) halo[i] = 0;
+      for (int i = tid; i < nrp; i += bd) halo[i] = 0u;
     for (int i = tid; i < wpad * pl.nrb; i += bd) pbits[i] = 0;
     for (int i = tid; i < wpad * R; i += bd) cnt[i] = 0;
     if (tid == 0) sh.flags = 0;
@@ -456,13 +952,18 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       sh.wide = 0;
     }
     __syncthreads();
-    stage_vote32(io.xy, a + h0, cn, hb, &sh.nv, &sh.wide);
+    stage_vote32(io.xy, a + h0, cn, hb, &sh.nv, &sh.wide, pl.fpbin != 0, pl.mp ? pl.mp_lsq : 0);
     __syncthreads();
     if (sh.wide & 2) {
       if (tid == 0) sh.flags |= HOUGH_F_BAD_HIT;
     }
     if (!(sh.wide & 1)) {
-      vote32<A32>(pl, acc, halo, hb, sh.nv, cj, sj, col_ok, halo_warp, hc, hs, g, p, lane);
+      if (pl.mp)
+        vote_mp32(pl, L, hb, sh.nv);
+      else if (pl.fpbin)
+        vote32_fp<A32>(pl, L, hb, sh.nv);
+      else
+        vote32<A32>(pl, L, hb, sh.nv);
     } else {
       const int half = pl.hit_cap >> 1;
       for (int s0 = 0; s0 < cn; s0 += half) {
@@ -472,74 +973,26 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
         __syncthreads();
         stage_vote64(io.xy, a + h0 + s0, sn, hw, &sh.nv);
         __syncthreads();
-        vote64<A32>(pl, acc, halo, hw, sh.nv, cj, sj, col_ok, halo_warp, hc, hs, g, p, lane);
+        if (pl.mp)
+          vote_mp64(pl, L, hw, sh.nv);
+        else
+          vote64<A32>(pl, L, hw, sh.nv);
       }
     }
   }
   __syncthreads();
 
-  // 3. peak scan: warps sweep 30-column blocks (lanes 0 and 31 only supply neighbour
-  // columns) over row ranges with a 3-row window; neighbour column maxima come by shuffle.
+  // 3. peak scan
   unsigned long long csum = 0;
-  {
-    const int nwarps = bd >> 5;
-    const int nblk = (wt + 29) / 30;
-    const int nunits = nblk * R;
-    for (int u = warp; u < nunits; u += nwarps) {
-      const int b = u / R, r = u % R;
-      const int k0 = (NR * r) / R, k1 = (NR * (r + 1)) / R;
-      const int c = b * 30 + lane - 1;
-      int kind = 0, scol = c;
-      bool mir = false;
-      if (c < 0) {
-        if (T == 1) {
-          scol = wt - 1;
-          mir = true;
-        } else {
-          kind = 1;
-          mir = (j0 == 0);
-        }
-      } else if (c >= wt) {
-        if (c == wt) {
-          if (T == 1) {
-            scol = 0;
-            mir = true;
-          } else {
-            kind = 2;
-            mir = (j0 + wt == NT);
-          }
-        } else {
-          kind = 3;
-        }
-      }
-      const bool tested = lane >= 1 && lane <= 30 && c >= 0 && c < wt;
-      const bool lstrict = !(c == 0 && j0 == 0);
-      const bool rstrict = (c == wt - 1) && (j0 + wt == NT);
-      auto fetch = [&](int kk) -> int {
-        const int rr = mir ? NR - 1 - kk : kk;
-        if (kind == 3 || rr < 0 || rr >= NR) return -1;
-        if (kind == 0) return acc_get<A32>(acc, scol, rr, nrp);
-        return halo[(kind - 1) * nrp + rr];
-      };
-      int vp = fetch(k0 - 1), vc = fetch(k0);
-      int cnt_l = 0;
-      const unsigned long long cell0 = (unsigned long long)(j0 + c) * NR;
-      for (int k = k0; k < k1; ++k) {
-        const int vn = fetch(k + 1);
-        const int vm = max(max(vp, vc), vn);
-        const int vmL = __shfl_up_sync(kFull, vm, 1);
-        const int vmR = __shfl_down_sync(kFull, vm, 1);
-        if (tested && vc >= pl.threshold && vc > vp && vc >= vn && (lstrict ? vc > vmL : vc >= vmL) &&
-            (rstrict ? vc > vmR : vc >= vmR)) {
-          atomicOr(&pbits[c * pl.nrb + (k >> 5)], 1u << (k & 31));
-          ++cnt_l;
-        }
-        if (do_cs && tested && vc > 0) csum += (unsigned long long)vc * mix64(cell0 + k + 1);
-        vp = vc;
-        vc = vn;
-      }
-      if (tested) cnt[c * R + r] = cnt_l;
-    }
+  const bool packed = !pl.mp && !A32 && (NR & 1) == 0;
+  if (pl.mp) {
+    mp_fold(pl, acc);
+    __syncthreads();
+    scan_mp(pl, acc, pbits, cnt, do_cs, csum);
+  } else if (packed) {
+    scan_packed(pl, acc, halo, pbits, cnt, wt, T, j0, do_cs, csum);
+  } else {
+    scan_scalar<A32>(pl, acc, halo, pbits, cnt, wt, T, j0, do_cs, csum);
   }
   __syncthreads();
 
@@ -549,7 +1002,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
   for (int key = tid; key < wt * R; key += bd) {
     const int c = key / R, r = key % R;
-    const int k0 = (NR * r) / R, k1 = (NR * (r + 1)) / R;
+    int k0, k1;
+    scan_rows(pl, packed, r, k0, k1);
     if (k0 >= k1) continue;
     int pos = cnt[key];
     for (int w = k0 >> 5; w <= ((k1 - 1) >> 5); ++w) {
@@ -564,7 +1018,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
           hough_peak pk;
           pk.theta_bin = (int16_t)(j0 + c);
           pk.rho_bin = (int16_t)k;
-          pk.votes = (int16_t)acc_get<A32>(acc, c, k, nrp);
+          pk.votes = (int16_t)(pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp));
           pk.flags = 0;
           dst[pos] = pk;
         }
@@ -711,7 +1165,46 @@ __global__ void __launch_bounds__(1024) prep_kernel(const long long* off, long l
   }
 }
 
+// Random (u, v, column) tuples in the int32 fast-path range: the float bin (with its exact
+// fallback) against plain 64-bit floor division. Counts disagreements and fallbacks.
+__global__ void selftest_fpbin_kernel(const Plan pl, const TrigTable trig, unsigned long long seed, long long n,
+                                      unsigned long long* out) {
+  unsigned long long bad = 0, amb = 0;
+  const FpBin K{pl.fp_khi, pl.fp_dlo, pl.fp_dhi};
+  const long long NR = pl.n_rho;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long z = mix64(seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1));
+    const int u = (int)(z % (2ULL * kFast32 + 1)) - kFast32;
+    const int v = (int)((z >> 20) % (2ULL * kFast32 + 1)) - kFast32;
+    const int j = (int)((z >> 44) % (unsigned long long)pl.n_theta);
+    const int c = trig.c[j], s = trig.s[j];
+    const float uf = (float)u, vf = (float)v;
+    const float A = __fmul_rn((float)c, pl.fp_scale), B = __fmul_rn((float)s, pl.fp_scale);
+    const float kf = __fmaf_rn(uf, A, __fmaf_rn(vf, B, pl.fp_c0));
+    const int k = bin_fp(kf, K, uf, vf, c, s, pl.magic);
+    const float kc = fminf(fmaxf(kf, 0.5f), K.khi);
+    amb += __fadd_rn(__fadd_rn(kc, K.dlo), 12582912.0f) != __fadd_rn(__fadd_rn(kc, K.dhi), 12582912.0f);
+    const long long t = (long long)u * c + (long long)v * s + kH;
+    const long long ref = t < 0 ? 0 : min(NR - 1, (t * NR) / (2 * kH));
+    bad += (k != ref);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    bad += __shfl_down_sync(kFull, bad, o);
+    amb += __shfl_down_sync(kFull, amb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicAdd(out, bad);
+    if (amb) atomicAdd(out + 1, amb);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_fpbin(const Plan& pl, const TrigTable& trig, unsigned long long seed, long long n,
+                                  unsigned long long* out, cudaStream_t st) {
+  selftest_fpbin_kernel<<<152 * 8, 256, 0, st>>>(pl, trig, seed, n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prep(const long long* off, long long n_events, long long n_hits, int* status,
                         unsigned long long* queue, int* tickets, int* order, cudaStream_t st) {

@@ -24,9 +24,16 @@ struct Plan {
   int hit_cap;    // hits staged in shared memory per chunk
   int scan_ranges;  // row ranges of the peak scan
   int grab;       // persistent queue: items per pop
-  int ctas_per_sm;
+  int mirror;     // 1: each vote lane owns column j and its mirror N_theta-1-j
+  int fpbin;      // 1: fast-path bins from a float estimate, exact integer path when ambiguous
+  int mp;         // 1: mirror-pair word layout (column j low half, N_theta-1-j high half, guard rows)
+  int rows_phys;  // mirror-pair layout: physical rows per column (N_rho + 2)
+  int mp_F, mp_pmask, mp_amb_add, mp_amb_lim, mp_fmask;  // bit extraction of the float row estimate
+  float mp_c0;    // N_rho/2 + 1 + 2^b
+  long long mp_lsq;  // fast path when u^2 + v^2 <= mp_lsq (rho within half a bin of the range)
+  float fp_scale, fp_c0, fp_khi, fp_dlo, fp_dhi;  // N_rho/2H, N_rho/2, N_rho-1/2, delta-1/2, -delta-1/2
   // shared-memory layout in bytes
-  int off_acc, region_bytes, off_halo, off_hits, off_pbits, off_cnt, off_trig, smem_bytes;
+  int off_acc, region_bytes, off_halo, off_hits, off_pbits, off_cnt, off_unres, off_trig, smem_bytes;
   BinMagic magic;
 };
 
@@ -77,6 +84,8 @@ cudaError_t launch_select(const long long* uq, const long long* vq, const long l
 cudaError_t launch_pack_peaks(const int* npeaks, const hough_peak* peaks, long long n_events, int max_peaks,
                               long long* peak_off, hough_peak* dense, cudaStream_t st);
 
+cudaError_t launch_selftest_fpbin(const Plan& pl, const TrigTable& trig, unsigned long long seed, long long n,
+                                  unsigned long long* out, cudaStream_t st);
 cudaError_t launch_selftest_bin(int n_rho, long long lo, long long hi, unsigned long long* mismatch, cudaStream_t st);
 cudaError_t launch_probe_atomics(int mode, int ctas_per_sm, int threads, int smem_bytes, int iters,
                                  unsigned long long* sink, cudaStream_t st);

@@ -258,8 +258,10 @@ __global__ void probe_kernel(int mode, int words, int iters, unsigned long long*
     } else if (mode == 1) {
       unsigned long long z = (unsigned long long)(blockIdx.x * 1315423911u + threadIdx.x * 2654435761u + r * 97u);
       w = (int)(mix64(z) % (unsigned long long)words);
-    } else {
+    } else if (mode == 2) {
       w = ((warp * 16 + r) % rows) * 32;
+    } else {
+      w = (warp % rows) * 32 + lane;  // mode 3: each thread keeps adding to one word of its own bank
     }
     p[r] = sm + w;
   }
