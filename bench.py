@@ -176,6 +176,31 @@ def probe_atomic_ceiling(h, torch, stream):
     return out
 
 
+def measure_serving(h, cfg, p, rates, seconds, pool_events=20000, seed=11):
+    """Continuous-batching server vs plain per-batch launches of 1,000 events on the same Poisson
+    arrival streams. Latency runs from each event's scheduled arrival to its results in host memory."""
+    pool = gen.generate(cfg, pool_events, with_truth=False)
+    rng = np.random.default_rng(seed)
+    out = []
+    for rate in rates:
+        n = int(rate * seconds)
+        arrival = np.cumsum(rng.exponential(1e9 / rate, size=n)).astype(np.int64)
+        row = {"offered_events_per_s": rate, "seconds": seconds, "events": n}
+        for name, kw in (("served", dict(slots=4, max_batch_events=256, flush_us=200.0)),
+                         ("plain_1000", dict(slots=1, max_batch_events=1000, flush_us=0.0))):
+            with h.Server(p, max_batch_hits=1 << 22, **kw) as srv:
+                t0 = srv.replay(pool.xy, pool.off, arrival)
+                srv.drain(120)
+                res = srv.poll_numpy(n + 16)
+            lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e3
+            span = (res["t_done_ns"].max() - t0) / 1e9 if len(res) else float("nan")
+            row[name] = {"sustained_events_per_s": len(res) / span, "p50_us": float(np.percentile(lat, 50)),
+                         "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
+                         "completed": int(len(res)), "flags": int(np.bitwise_or.reduce(res["status"]))}
+        out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,6 +213,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle events for cpu_baseline")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline (profiling runs)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each serving stream")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     cfg = gen.CONFIGS[args.workload]
     if args.impl == "reference":
@@ -315,6 +342,12 @@ def main():
         cpu = {"value": v, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"first {n} events of this batch ({dt:.1f} s wall on {threads} threads)"}
 
+    served = None
+    if not args.no_serve:
+        scfg = gen.CONFIGS["served"]
+        served = measure_serving(h, scfg, h.params(scfg.n_theta, scfg.n_rho, scfg.threshold, scfg.keep_halfwidth,
+                                                   scfg.max_peaks), (50_000, 200_000, 400_000), args.serve_seconds)
+
     import oracle
     rc, rs = oracle.metrics(out.mask.cpu().numpy(), ev.truth) if ev.truth is not None else (None, None)
     line = {
@@ -330,6 +363,7 @@ def main():
                    "parallelism": f"events sharded over {ws} GPU(s)"},
         "hits_per_s": ev.n_hits * ws * args.steps / (elapsed * 1e-3),
         "latency": {"batch_ms": ms_step, "note": "every event of the batch completes within one step"},
+        "served": served,
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "kernel": "fused_kernel (persistent)", "achieved": achieved, "peak": alu_peak,

@@ -167,6 +167,69 @@ size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_e
  * with cudaEventElapsedTime. NULL, NULL turns it off. Graph replays are cached per pair. */
 void hough_set_stage_events(void* begin, void* end);
 
+/* ---- serving loop (continuous batching) ---- */
+
+/* Configuration of a serving loop. Requests (one event each) are admitted into micro-batches;
+ * up to `slots` micro-batches are in flight at once, each on its own stream with its own
+ * device and pinned host buffers, so new arrivals are gathered while earlier ones run. A
+ * micro-batch is launched when it holds max_batch_events events or max_batch_hits hits, or
+ * when its oldest request has waited flush_ns (0: only when full, or on drain). */
+typedef struct hough_serve_config {
+  hough_params params;
+  int32_t slots;            /* micro-batches in flight, 1..64 */
+  int32_t max_batch_events; /* events per micro-batch, >= 1 */
+  int64_t max_batch_hits;   /* hits per micro-batch, >= 1 (also the largest admissible event) */
+  int64_t flush_ns;         /* longest wait of a request before its partial batch is launched */
+  int32_t queue_capacity;   /* requests waiting for a slot before submit refuses (HOUGH_EFULL) */
+  int32_t reserved;
+} hough_serve_config;
+
+/* One finished request. Latency = t_done_ns - t_arrival_ns (steady clock, ns): from the
+ * request's arrival (its submit call, or its scheduled time in hough_serve_replay) to the
+ * moment its results were in host memory. */
+typedef struct hough_serve_result {
+  int64_t id;
+  int32_t status; /* HOUGH_F_* flags raised by the micro-batch the request ran in */
+  int32_t npeaks; /* true peak count */
+  int32_t nkept;  /* kept hits */
+  int32_t reserved;
+  int64_t t_arrival_ns;
+  int64_t t_done_ns;
+} hough_serve_result;
+
+/* Device and pinned-host bytes a server with this configuration needs. */
+int hough_serve_buffer_sizes(const hough_serve_config* c, size_t* device_bytes, size_t* pinned_bytes);
+
+/* Starts a server on the current device. d_buf (device) and h_pinned (page-locked host
+ * memory) are caller-owned, 256-byte aligned and must outlive the server. *server receives
+ * an opaque handle. A host thread owned by the server runs the loop until hough_serve_close. */
+int hough_serve_open(const hough_serve_config* c, void* d_buf, size_t d_bytes, void* h_pinned, size_t h_bytes,
+                     void** server);
+
+/* Admits one event (h_xy: n_hits interleaved int32 (x, y) pairs, read when its micro-batch is
+ * gathered, so it must stay valid until the request completes). On completion its kept mask
+ * (n_hits bytes) and stored peaks (up to max_peaks records) are copied to h_mask_out /
+ * h_peaks_out when non-NULL. Returns HOUGH_EFULL when queue_capacity requests are waiting. */
+int hough_serve_submit(void* server, const int32_t* h_xy, int64_t n_hits, int64_t id, uint8_t* h_mask_out,
+                       hough_peak* h_peaks_out);
+
+/* Moves up to max_results finished requests into out; *n_out gets the count. */
+int hough_serve_poll(void* server, hough_serve_result* out, int32_t max_results, int32_t* n_out);
+
+/* Launches any partial micro-batch and waits until every admitted request has finished, or
+ * timeout_ns elapsed (HOUGH_ETIMEDOUT). */
+int hough_serve_drain(void* server, int64_t timeout_ns);
+
+/* Replays an arrival schedule from the calling thread: request i is event (i mod pool_events)
+ * of the pool (h_off_pool offsets into h_xy_pool) and is submitted at t0 + arrival_ns[i]
+ * (busy wait), t0 written to *t_start_ns. A refused admission is retried for up to 10 s with
+ * the same scheduled arrival time. Results are not copied out (only counted and timed). */
+int hough_serve_replay(void* server, const int32_t* h_xy_pool, const int64_t* h_off_pool, int64_t pool_events,
+                       const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns);
+
+/* Stops the loop, waits for the streams and releases the handle. */
+int hough_serve_close(void* server);
+
 /* Size of the library's built-in scratch array used by hough_run_batched_static. */
 #define HOUGH_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

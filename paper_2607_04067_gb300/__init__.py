@@ -43,6 +43,18 @@ class Params(ctypes.Structure):
         return "Params(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("params", Params), ("slots", ctypes.c_int32), ("max_batch_events", ctypes.c_int32),
+                ("max_batch_hits", ctypes.c_int64), ("flush_ns", ctypes.c_int64), ("queue_capacity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("npeaks", ctypes.c_int32),
+                ("nkept", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t_arrival_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
 def params(n_theta: int, n_rho: int, threshold: int, keep_halfwidth: int = 1, max_peaks: int = 1024,
            theta_tiles: int = 0, events_per_cta: int = 0, block: int = 0) -> Params:
     return Params(n_theta, n_rho, threshold, keep_halfwidth, max_peaks, theta_tiles, events_per_cta, block)
@@ -86,6 +98,19 @@ def load(build: bool = True):
                 fn.restype = ctypes.c_int
             lib.hough_workspace_size.argtypes = [P, i64]
             lib.hough_workspace_size.restype = ctypes.c_size_t
+            SP = ctypes.POINTER(ServeConfig)
+            for name, args in {
+                "hough_serve_buffer_sizes": [SP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+                "hough_serve_open": [SP, vp, ctypes.c_size_t, vp, ctypes.c_size_t, ctypes.POINTER(vp)],
+                "hough_serve_submit": [vp, vp, i64, i64, vp, vp],
+                "hough_serve_poll": [vp, vp, i32, ctypes.POINTER(i32)],
+                "hough_serve_drain": [vp, i64],
+                "hough_serve_replay": [vp, vp, vp, i64, vp, i64, ctypes.POINTER(i64)],
+                "hough_serve_close": [vp],
+            }.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
             lib.hough_host_buffer_size.argtypes = [P, i64, i64]
             lib.hough_host_buffer_size.restype = ctypes.c_size_t
             lib.hough_set_stage_events.argtypes = [vp, vp]
@@ -302,6 +327,80 @@ class HostRunner:
             return int(self.status[0].item())
         _check("hough_run_host", rc)
         return 0
+
+
+class Server:
+    """Continuous-batching serving loop (``hough_serve_*``). The device and pinned buffers are
+    torch tensors owned by this object; the loop itself is a native thread in the library."""
+
+    def __init__(self, p: Params, slots: int = 4, max_batch_events: int = 256, max_batch_hits: int = 1 << 20,
+                 flush_us: float = 200.0, queue_capacity: int = 1 << 20, device="cuda"):
+        torch = _torch()
+        self.cfg = ServeConfig(p, slots, max_batch_events, max_batch_hits, int(flush_us * 1000), queue_capacity, 0)
+        lib = load()
+        db, hb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check("hough_serve_buffer_sizes", lib.hough_serve_buffer_sizes(ctypes.byref(self.cfg), ctypes.byref(db),
+                                                                         ctypes.byref(hb)))
+        self.dbuf = torch.empty(db.value + 256, dtype=torch.uint8, device=device)
+        self.hbuf = torch.empty(hb.value + 256, dtype=torch.uint8).pin_memory()
+        d0 = (-self.dbuf.data_ptr()) % 256
+        h0 = (-self.hbuf.data_ptr()) % 256
+        self.handle = ctypes.c_void_p()
+        _check("hough_serve_open", lib.hough_serve_open(
+            ctypes.byref(self.cfg), ctypes.c_void_p(self.dbuf.data_ptr() + d0), db.value,
+            ctypes.c_void_p(self.hbuf.data_ptr() + h0), hb.value, ctypes.byref(self.handle)))
+
+    def submit(self, xy_host, req_id: int, mask_out=None, peaks_out=None) -> int:
+        """xy_host: contiguous int32 [n, 2] CPU tensor/array kept alive until completion."""
+        ptr = xy_host.data_ptr() if hasattr(xy_host, "data_ptr") else xy_host.ctypes.data
+        n = xy_host.shape[0]
+        mo = None if mask_out is None else ctypes.c_void_p(
+            mask_out.data_ptr() if hasattr(mask_out, "data_ptr") else mask_out.ctypes.data)
+        po = None if peaks_out is None else ctypes.c_void_p(
+            peaks_out.data_ptr() if hasattr(peaks_out, "data_ptr") else peaks_out.ctypes.data)
+        return load().hough_serve_submit(self.handle, ctypes.c_void_p(ptr), n, req_id, mo, po)
+
+    def poll(self, max_results: int = 1 << 16):
+        buf = (ServeResult * max_results)()
+        n = ctypes.c_int32()
+        rc = load().hough_serve_poll(self.handle, buf, max_results, ctypes.byref(n))
+        if rc:
+            raise HoughError("hough_serve_poll", rc)
+        return [buf[i] for i in range(n.value)]
+
+    def poll_numpy(self, max_results: int = 1 << 22):
+        import numpy as np
+        dt = np.dtype([("id", "<i8"), ("status", "<i4"), ("npeaks", "<i4"), ("nkept", "<i4"), ("reserved", "<i4"),
+                       ("t_arrival_ns", "<i8"), ("t_done_ns", "<i8")])
+        out = np.zeros(max_results, dt)
+        n = ctypes.c_int32()
+        rc = load().hough_serve_poll(self.handle, ctypes.c_void_p(out.ctypes.data), max_results, ctypes.byref(n))
+        if rc:
+            raise HoughError("hough_serve_poll", rc)
+        return out[: n.value]
+
+    def drain(self, timeout_s: float = 30.0):
+        _check("hough_serve_drain", load().hough_serve_drain(self.handle, int(timeout_s * 1e9)))
+
+    def replay(self, xy_pool, off_pool, arrival_ns) -> int:
+        """Submits request i = pool event i mod n at its scheduled time; returns t0 (ns)."""
+        t0 = ctypes.c_int64()
+        _check("hough_serve_replay", load().hough_serve_replay(
+            self.handle, ctypes.c_void_p(xy_pool.ctypes.data), ctypes.c_void_p(off_pool.ctypes.data),
+            len(off_pool) - 1, ctypes.c_void_p(arrival_ns.ctypes.data), len(arrival_ns), ctypes.byref(t0)))
+        return t0.value
+
+    def close(self):
+        if self.handle:
+            rc = load().hough_serve_close(self.handle)
+            self.handle = ctypes.c_void_p()
+            _check("hough_serve_close", rc)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def set_stage_events(begin=None, end=None):

@@ -179,14 +179,14 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       pl.mp_fmask = (1 << F) - 1;
       pl.mp_amb_add = (int)std::ceil(p->n_rho * std::ldexp(1.0, F - 20)) + 1;
       pl.mp_amb_lim = 2 * pl.mp_amb_add;
-      pl.mp_c0 = (float)(0.5 * p->n_rho + 1.0 + (double)(1 << b));
+      pl.mp_c0 = (float)(0.5 * p->n_rho + 1.0 + (double)(1 << b) + std::ldexp((double)pl.mp_amb_add, -F));
       const double L = (double)kH * (1.0 + 1.0 / p->n_rho) / 16385.0;
       pl.mp_lsq = (long long)std::floor(L * L);
     }
-    int R = 4096 / (pl.groups * 32);
-    if (R < 1) R = 1;
-    if (R > 32) R = 32;
-    if (R > p->n_rho) R = p->n_rho;
+    // row ranges of the peak scan: a power of two (at most 32, at most 4096 counters) that
+    // divides N_rho, so every range has the same number of rows
+    int R = 1;
+    while (R < 32 && R * 2 * pl.groups * 32 <= 4096 && p->n_rho % (R * 2) == 0) R *= 2;
     pl.scan_ranges = R;
     for (int cap = 4096; cap >= 512; cap >>= 1) {
       pl.hit_cap = cap;

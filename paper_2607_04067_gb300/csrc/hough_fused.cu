@@ -25,7 +25,7 @@ namespace hgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSelCap = 4;  // peak columns a lane tries alone before its hit goes to a whole warp
+constexpr int kSelCap = 8;  // peak columns a lane tries alone before its hit goes to a whole warp
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -378,14 +378,15 @@ __device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, const P
   return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
 }
 
-// Byte offset of the row of the vote whose float estimate, shifted by 1 + 2^b (2^b > N_rho + 1),
-// is kfp. In [2^b, 2^(b+1)) a float's low F = 23 - b bits are the fraction and the bits above
-// them the integer part, so both come straight from the bit pattern. The estimate is within
-// N_rho 2^-21 + 2^-(F+1) of the exact value; if the fraction is within amb_add / 2^F of an
-// integer the exact integer path (clamped) decides.
+// Byte offset of the row of the vote whose float estimate, shifted by 1 + 2^b + e (2^b > N_rho + 1,
+// e = amb_add 2^-F), is kfp. In [2^b, 2^(b+1)) a float's low F = 23 - b bits are the fraction
+// and the bits above them the integer part, so both come straight from the bit pattern. The
+// estimate is within N_rho 2^-21 + 2^-(F+1) < e of the exact value; when the shifted fraction
+// is below 2e (the exact value within e of an integer) the exact integer path (clamped) decides,
+// otherwise the shift by e does not move the integer part.
 __device__ __forceinline__ uint32_t mp_row_off(float kfp, const Plan& pl, float uf, float vf, int c, int s) {
   const uint32_t y = (uint32_t)__float_as_int(kfp);
-  if (((y + (uint32_t)pl.mp_amb_add) & (uint32_t)pl.mp_fmask) < (uint32_t)pl.mp_amb_lim) {
+  if ((y & (uint32_t)pl.mp_fmask) < (uint32_t)pl.mp_amb_lim) {
     const int u = __float2int_rn(uf), v = __float2int_rn(vf);
     return (uint32_t)(rho_bin32(u * c + (v * s + (int)kH), pl.magic) + 1) << 7;
   }
@@ -439,6 +440,8 @@ __device__ void mp_fold(const Plan& pl, uint32_t* acc) {
     uint32_t* col = acc + mp_word(w, 0, rp);
     col[32] += col[0];
     col[NR << 5] += col[(NR + 1) << 5];
+    col[0] = 0u;  // zero guard rows now read as "no neighbour" in the scan
+    col[(NR + 1) << 5] = 0u;
   }
 }
 
@@ -453,43 +456,47 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, in
   const int nblk = (half + 29) / 30;
   const uint32_t TT = (uint32_t)pl.threshold | ((uint32_t)pl.threshold << 16);
   for (int u = warp; u < nblk * R; u += nwarps) {
-    const int b = u / R, r = u % R;
+    const int b = u / R, r = u - b * R;
     const int k0 = (NR * r) / R, k1 = (NR * (r + 1)) / R;
     const int w = b * 30 + lane - 1;
-    int sw = w;
-    bool mir = false, swp = false, none = false;
+    // Source word of this lane for logical row k: physical row k + 1 (or N_rho - k when the
+    // rows are mirrored); the zeroed guard rows supply the missing rows -1 and N_rho.
+    int sw = w, p0 = k0, step = 32;
+    unsigned sel = 0x3210u;  // byte permutation: identity, or swap of the two halves
     if (w < 0) {
       sw = 0;
-      mir = true;
-      swp = true;
+      p0 = NR - (k0 - 1);
+      step = -32;
+      sel = 0x1032u;
     } else if (w >= half) {
       if (w == half) {
         sw = half - 1;
-        swp = true;
+        sel = 0x1032u;
       } else {
-        none = true;
-        sw = 0;
+        sw = 0;  // nothing: read guard row 0 (zero) throughout
+        p0 = 0;
+        step = 0;
       }
     }
-    const uint32_t* col = acc + mp_word(sw, 1, rp);  // physical row 1 = logical row 0
-    auto fetch = [&](int k) -> uint32_t {
-      if (none || k < 0 || k >= NR) return 0u;
-      const uint32_t x = col[(mir ? NR - 1 - k : k) << 5];
-      return swp ? swap16(x) : x;
-    };
+    const uint32_t* ptr = acc + mp_word(sw, p0, rp);  // row k0 - 1
     const bool tested = lane >= 1 && lane <= 30 && w >= 0 && w < half;
     const bool lo_lstrict = (w != 0), hi_rstrict = (w == 0);
     const int clo = w, chi = NT - 1 - w;
-    uint32_t U = fetch(k0 - 1), C = fetch(k0);
+    uint32_t U = __byte_perm(ptr[0], 0u, sel);
+    ptr += step;
+    uint32_t C = __byte_perm(ptr[0], 0u, sel);
+    ptr += step;
     int n_lo = 0, n_hi = 0;
+#pragma unroll 2
     for (int k = k0; k < k1; ++k) {
-      const uint32_t D = fetch(k + 1);
+      const uint32_t D = __byte_perm(ptr[0], 0u, sel);
+      ptr += step;
       const uint32_t VM = vmax2(vmax2(U, C), D);
       const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
       const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
-      if (tested) {
-        const uint32_t X = vmax2(vmax2(vmax2(U, D), vmax2(VU, VD)), TT);
-        const uint32_t Y = vmax2(X, C) ^ C;  // half is 0 where C >= every neighbour and T
+      const uint32_t X = vmax2(vmax2(vmax2(U, D), vmax2(VU, VD)), TT);
+      const uint32_t Y = vmax2(X, C) ^ C;  // half is 0 where C >= every neighbour and T
+      if (tested && ((Y & 0xffffu) == 0u || (Y >> 16) == 0u)) {
         if ((Y & 0xffffu) == 0u) {
           const int a = C & 0xffff;
           if (a > (int)(U & 0xffff) && (!lo_lstrict || a > (int)(VU & 0xffff))) {
@@ -504,11 +511,11 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, in
             ++n_hi;
           }
         }
-        if (do_cs) {
-          const unsigned a0 = C & 0xffffu, a1 = C >> 16;
-          if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)clo * NR + k + 1);
-          if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)chi * NR + k + 1);
-        }
+      }
+      if (do_cs && tested) {
+        const unsigned a0 = C & 0xffffu, a1 = C >> 16;
+        if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)clo * NR + k + 1);
+        if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)chi * NR + k + 1);
       }
       U = C;
       C = D;
