@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each serving stream")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
+    ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
     args = ap.parse_args()
     cfg = gen.CONFIGS[args.workload]
     if args.impl == "reference":
@@ -240,6 +242,10 @@ def main():
     xy = torch.from_numpy(ev.xy).cuda()
     off = torch.from_numpy(ev.off).cuda()
     p = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks)
+    tune_ms = None
+    if not args.no_tune:
+        ns = min(n_events, args.tune_events)
+        p, tune_ms = h.autotune(xy[: int(ev.off[ns])], off[: ns + 1], p)
     plan = h.resolve(p)
     out = h.alloc_outputs(ev.n_hits, ev.n_events, p)
     stream = torch.cuda.Stream()
@@ -357,7 +363,9 @@ def main():
         "config": {"workload": cfg.name, "events_per_gpu": n_events, "hits_per_gpu": ev.n_hits,
                    "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
                    "max_peaks": cfg.max_peaks, "launch": {"theta_tiles": plan.theta_tiles, "block": plan.block,
-                                                          "events_per_cta": plan.events_per_cta},
+                                                          "events_per_cta": plan.events_per_cta,
+                                                          "autotuned": not args.no_tune,
+                                                          "tune_best_ms": tune_ms},
                    "path": "hough_run_batched (persistent kernel + CUDA graph)",
                    "l2": f"inputs {ev.xy.nbytes / 1e9:.2f} GB > 129 MB L2, no flush",
                    "parallelism": f"events sharded over {ws} GPU(s)"},

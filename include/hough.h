@@ -251,6 +251,18 @@ int hough_run_batched_static(const int32_t* d_xy, int64_t n_hits, const int64_t*
                              const hough_params* p, int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask,
                              int32_t* d_nkept, uint64_t* d_checksum, int32_t* d_status, void* stream);
 
+/* Autotuner of the batched path: times hough_run_batched's kernels on the sample batch
+ * (d_xy, d_off: device, the caller's representative events) for every feasible launch shape
+ * -- theta tiles in {1, 2, 4, 8, 16}, threads per CTA in {256, 512, 1024} (or the widest the
+ * tiling allows), queue items per pop (events_per_cta) in {1, 2, 4} -- and writes the fastest
+ * into *p (theta_tiles, block, events_per_cta; the algorithm fields are untouched). d_scratch
+ * holds outputs and workspace of every candidate: hough_autotune_scratch_size bytes, 256-byte
+ * aligned. Results are cached per (parameters, device, SM count, hits per event in octaves);
+ * a cached answer returns at once with *best_ms = -1. Synchronises `stream`. */
+size_t hough_autotune_scratch_size(const hough_params* p, int64_t n_hits, int64_t n_events);
+int hough_autotune(hough_params* p, const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                   void* d_scratch, size_t scratch_bytes, int32_t* d_status, void* stream, float* best_ms);
+
 /* Launch shape the library would use for these parameters: fills the zero launch fields
  * of *p (theta_tiles, events_per_cta, block) and returns HOUGH_OK or an error. */
 int hough_resolve_params(hough_params* p);

@@ -91,6 +91,7 @@ def load(build: bool = True):
                 "hough_probe_smem_atomics": [i32, i32, i32, i32, i32, vp, vp],
                 "hough_run_host": [vp, i64, vp, i64, P, vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp, vp],
                 "hough_run_batched_static": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, vp],
+                "hough_autotune": [P, vp, i64, vp, i64, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(ctypes.c_float)],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -111,6 +112,8 @@ def load(build: bool = True):
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+            lib.hough_autotune_scratch_size.argtypes = [P, i64, i64]
+            lib.hough_autotune_scratch_size.restype = ctypes.c_size_t
             lib.hough_host_buffer_size.argtypes = [P, i64, i64]
             lib.hough_host_buffer_size.restype = ctypes.c_size_t
             lib.hough_set_stage_events.argtypes = [vp, vp]
@@ -407,6 +410,22 @@ def set_stage_events(begin=None, end=None):
     """Records torch.cuda.Event pairs around the fused kernel of later calls on this thread."""
     load().hough_set_stage_events(ctypes.c_void_p(begin.cuda_event) if begin is not None else None,
                                   ctypes.c_void_p(end.cuda_event) if end is not None else None)
+
+
+def autotune(xy, off, p: Params, stream=None):
+    """Fastest launch shape for p on this sample batch (device tensors): (tuned Params, ms or -1 if cached)."""
+    torch = _torch()
+    xy = _dev(xy, "xy", torch.int32)
+    off = _dev(off, "off", torch.int64)
+    q = Params(*[getattr(p, n) for n, _ in Params._fields_])
+    lib = load()
+    nb = int(lib.hough_autotune_scratch_size(ctypes.byref(q), xy.shape[0], off.shape[0] - 1))
+    scratch = torch.empty(nb, dtype=torch.uint8, device=xy.device)
+    st = new_status(xy.device)
+    ms = ctypes.c_float()
+    _check("hough_autotune", lib.hough_autotune(ctypes.byref(q), _ptr(xy), xy.shape[0], _ptr(off), off.shape[0] - 1,
+                                                _ptr(scratch), nb, _ptr(st), _stream(stream), ctypes.byref(ms)))
+    return q, float(ms.value)
 
 
 def selftest_bin(n_rho: int, rho_lo: int, rho_hi: int, stream=None) -> int:

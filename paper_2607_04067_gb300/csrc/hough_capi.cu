@@ -2,7 +2,9 @@
 // replay of the batched path, status words. See include/hough.h for the contract.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <list>
+#include <map>
 #include <mutex>
 
 #include "hough_internal.h"
@@ -397,6 +399,145 @@ static int enqueue_batched(const Common& cm0, const hough_params* p, int64_t n_h
   cm.io.persistent = 1;
   e = timed_fused(cm.pl, cm.io, trig, grid, st);
   return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
+// ---- autotuner ----
+
+namespace {
+
+struct TuneKey {
+  int n_theta, n_rho, threshold, keep_hw, max_peaks, device, sms, hits_bucket;
+  bool operator<(const TuneKey& o) const { return std::memcmp(this, &o, sizeof(TuneKey)) < 0; }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, hough_params> g_tune_cache;
+
+struct TuneScratch {
+  size_t npeaks, peaks, mask, nkept, ws, total;
+};
+
+TuneScratch tune_scratch(const hough_params* p, int64_t n_hits, int64_t n_events) {
+  TuneScratch L{};
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t at = o;
+    o = (o + (b ? b : 1) + 255) & ~(size_t)255;
+    return at;
+  };
+  L.npeaks = take(4 * (size_t)n_events);
+  L.peaks = take(sizeof(hough_peak) * (size_t)n_events * (size_t)p->max_peaks);
+  L.mask = take((size_t)n_hits);
+  L.nkept = take(4 * (size_t)n_events);
+  size_t ws = 0;
+  for (int T = 1; T <= 16; T *= 2) {
+    hough_params q = *p;
+    q.theta_tiles = T;
+    q.block = 0;
+    Plan pl;
+    if (make_plan(&q, pl) == HOUGH_OK) ws = std::max(ws, ws_layout(pl, n_events).total);
+  }
+  L.ws = take(ws);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+size_t hough_autotune_scratch_size(const hough_params* p, int64_t n_hits, int64_t n_events) {
+  if (check_params(p) != HOUGH_OK || n_hits < 0 || n_events < 0) return 256;
+  return tune_scratch(p, n_hits, n_events).total;
+}
+
+int hough_autotune(hough_params* p, const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,
+                   void* d_scratch, size_t scratch_bytes, int32_t* d_status, void* stream, float* best_ms) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!d_off || !d_scratch || !d_status || n_events < 1 || n_hits < 0 || ((uintptr_t)d_scratch & 255))
+    return HOUGH_EINVAL;
+  const TuneScratch L = tune_scratch(p, n_hits, n_events);
+  if (scratch_bytes < L.total) return HOUGH_EWORKSPACE;
+  TuneKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.n_theta = p->n_theta;
+  key.n_rho = p->n_rho;
+  key.threshold = p->threshold;
+  key.keep_hw = p->keep_halfwidth;
+  key.max_peaks = p->max_peaks;
+  cudaGetDevice(&key.device);
+  cudaDeviceGetAttribute(&key.sms, cudaDevAttrMultiProcessorCount, key.device);
+  {
+    const double hpe = (double)n_hits / (double)n_events;  // hit density in octaves
+    int b = 0;
+    while (b < 20 && (double)(1 << (b + 1)) <= hpe) ++b;
+    key.hits_bucket = b;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *p = it->second;
+      if (best_ms) *best_ms = -1.0f;
+      return HOUGH_OK;
+    }
+  }
+  char* s = (char*)d_scratch;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  hough_params best = *p;
+  float best_t = 1e30f;
+  bool found = false;
+  for (int T = 1; T <= 16; T *= 2) {
+    for (int threads : {256, 512, 1024}) {
+      for (int grab : {1, 2, 4}) {
+        hough_params q = *p;
+        q.theta_tiles = T;
+        q.events_per_cta = grab;
+        Plan probe;
+        q.block = 0;
+        if (make_plan(&q, probe) != HOUGH_OK) continue;
+        const int halo = T > 1 ? 32 : 0;
+        const int lanes = probe.groups * 32;
+        if (threads - halo <= 0 || (threads - halo) % lanes) {
+          if (threads != 1024) continue;
+          q.block = probe.threads;  // the widest block this tiling allows
+        } else {
+          q.block = threads;
+        }
+        Common cm;
+        if (prepare_fused(d_xy, n_hits, d_off, n_events, &q, (int32_t*)(s + L.npeaks), (hough_peak*)(s + L.peaks),
+                          (uint8_t*)(s + L.mask), (int32_t*)(s + L.nkept), nullptr, s + L.ws,
+                          scratch_bytes - L.ws, d_status, cm) != HOUGH_OK)
+          continue;
+        const int grid = batched_grid(cm);
+        if (grid < 1) continue;
+        if (enqueue_batched(cm, &q, n_hits, n_events, s + L.ws, d_status, grid, st) != HOUGH_OK) continue;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2; ++r) enqueue_batched(cm, &q, n_hits, n_events, s + L.ws, d_status, grid, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms *= 0.5f;
+        if (ms < best_t) {
+          best_t = ms;
+          best = q;
+          found = true;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!found) return HOUGH_ESMEM;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  *p = best;
+  if (best_ms) *best_ms = best_t;
+  return HOUGH_OK;
 }
 
 int hough_run_batched(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,

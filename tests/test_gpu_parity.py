@@ -314,6 +314,21 @@ def test_float_bin_path_random_tuples(h, n_theta, n_rho):
     assert 0 < amb < 200_000_000 * 4e-3  # the fallback is exercised, and rare
 
 
+def test_autotuned_shape_gives_identical_results(h):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 200)
+    xy, off = dev(ev)
+    p = cfg_params(h, cfg)
+    tuned, ms = h.autotune(xy, off, p)
+    assert ms > 0 and tuned.theta_tiles >= 1 and tuned.block % 32 == 0 and tuned.events_per_cta >= 1
+    again, ms2 = h.autotune(xy, off, p)  # cached
+    assert ms2 == -1.0 and [getattr(again, f) for f, _ in again._fields_] == [getattr(tuned, f) for f, _ in tuned._fields_]
+    ref = oracle_of(cfg, ev)
+    out = h.run(xy, off, tuned, checksum=True, batched=True)
+    assert h.status(out.status) == 0
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, checksum=out.checksum)
+
+
 def test_host_errors(h):
     xy = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
     off = torch.tensor([0, 4], dtype=torch.int64, device="cuda")
