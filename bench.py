@@ -217,6 +217,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
+    ap.add_argument("--shape", default="", help="fixed launch shape 'theta_tiles,block,events_per_cta' (profiling)")
     args = ap.parse_args()
     cfg = gen.CONFIGS[args.workload]
     if args.impl == "reference":
@@ -243,7 +244,9 @@ def main():
     off = torch.from_numpy(ev.off).cuda()
     p = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks)
     tune_ms = None
-    if not args.no_tune:
+    if args.shape:
+        p.theta_tiles, p.block, p.events_per_cta = (int(x) for x in args.shape.split(","))
+    elif not args.no_tune:
         ns = min(n_events, args.tune_events)
         p, tune_ms = h.autotune(xy[: int(ev.off[ns])], off[: ns + 1], p)
     plan = h.resolve(p)
@@ -364,7 +367,7 @@ def main():
                    "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
                    "max_peaks": cfg.max_peaks, "launch": {"theta_tiles": plan.theta_tiles, "block": plan.block,
                                                           "events_per_cta": plan.events_per_cta,
-                                                          "autotuned": not args.no_tune,
+                                                          "autotuned": not (args.no_tune or args.shape),
                                                           "tune_best_ms": tune_ms},
                    "path": "hough_run_batched (persistent kernel + CUDA graph)",
                    "l2": f"inputs {ev.xy.nbytes / 1e9:.2f} GB > 129 MB L2, no flush",

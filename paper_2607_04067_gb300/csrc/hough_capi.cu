@@ -75,7 +75,7 @@ static bool layout(Plan& pl) {
   const int wpad = pl.groups * 32;
   const int cell = pl.acc32 ? 4 : 2;
   const int acc_bytes = pl.mp ? (pl.n_theta / 2) * pl.rows_phys * 4 : wpad * pl.nrho_pad * cell;
-  const int sel_bytes = (2 * pl.n_theta + 64) * 4 + pl.n_theta * 8 + pl.n_theta * pl.nrb * 4;
+  const int sel_bytes = (2 * pl.n_theta + 64) * 4 + pl.n_theta * 16 + pl.n_theta * pl.nrb_g * 4;
   int o = 0;
   pl.off_acc = o;
   pl.region_bytes = round16(acc_bytes > sel_bytes ? acc_bytes : sel_bytes);
@@ -84,6 +84,8 @@ static bool layout(Plan& pl) {
   if (pl.tiles > 1) o += round16(2 * pl.nrho_pad * 4);
   pl.off_hits = o;
   o += round16(pl.hit_cap * 8);
+  pl.off_idx = o;
+  if (pl.mp) o += round16(pl.hit_cap * 2);
   pl.off_pbits = o;
   o += round16(wpad * pl.nrb * 4);
   pl.off_cnt = o;
@@ -119,6 +121,7 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
   pl.keep_hw = p->keep_halfwidth;
   pl.max_peaks = p->max_peaks;
   pl.nrb = (p->n_rho + 31) / 32;
+  pl.nrb_g = (p->n_rho + 2 + 31) / 32;
   pl.magic = host_magic(p->n_rho);
   pl.grab = p->events_per_cta > 0 ? p->events_per_cta : 1;
   {
@@ -188,8 +191,13 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
     // row ranges of the peak scan: a power of two (at most 32, at most 4096 counters) that
     // divides N_rho, so every range has the same number of rows
     int R = 1;
-    while (R < 32 && R * 2 * pl.groups * 32 <= 4096 && p->n_rho % (R * 2) == 0) R *= 2;
+    int Rs = 0;
+    while (R < 32 && R * 2 * pl.groups * 32 <= 4096 && p->n_rho % (R * 2) == 0) {
+      R *= 2;
+      ++Rs;
+    }
     pl.scan_ranges = R;
+    pl.scan_shift = Rs;
     for (int cap = 4096; cap >= 512; cap >>= 1) {
       pl.hit_cap = cap;
       if (layout(pl)) return HOUGH_OK;

@@ -130,7 +130,7 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
 // (compacted, order not kept). Valid hits beyond int32 set bit 0 of *s_flags, bad
 // hits bit 1.
 __device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn, int2* hb, int* s_nv, int* s_flags,
-                             bool as_float, long long lsq) {
+                             bool as_float, long long lsq, uint16_t* idx) {
   const int lane = threadIdx.x & 31;
   for (int i0 = 0; i0 < cn; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
@@ -150,9 +150,11 @@ __device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn
       if (lane == 0) slot = atomicAdd(s_nv, __popc(bal));
       slot = __shfl_sync(kFull, slot, 0);
       // float form for the float bin path: |u|, |v| <= 44061 are exact in float
-      if (f)
-        hb[slot + __popc(bal & lanemask_lt())] =
-            as_float ? make_int2(__float_as_int((float)u), __float_as_int((float)v)) : make_int2((int)u, (int)v);
+      if (f) {
+        const int at = slot + __popc(bal & lanemask_lt());
+        hb[at] = as_float ? make_int2(__float_as_int((float)u), __float_as_int((float)v)) : make_int2((int)u, (int)v);
+        if (idx) idx[at] = (uint16_t)i;
+      }
     }
     if (ok && !f) atomicOr(s_flags, 1);
     if (st) atomicOr(s_flags, 2);
@@ -404,7 +406,7 @@ __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, con
   const uint32_t base = L.col1;
   const float4* hb4 = reinterpret_cast<const float4*>(hb);
   const int np = nv >> 1, P = L.P;
-#pragma unroll 2
+#pragma unroll 4
   for (int q = L.p; q < np; q += P) {
     const float4 h = hb4[q];
     const float v0 = __fmaf_rn(h.y, B, c0), v1 = __fmaf_rn(h.w, B, c0);
@@ -456,8 +458,8 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, in
   const int nblk = (half + 29) / 30;
   const uint32_t TT = (uint32_t)pl.threshold | ((uint32_t)pl.threshold << 16);
   for (int u = warp; u < nblk * R; u += nwarps) {
-    const int b = u / R, r = u - b * R;
-    const int k0 = (NR * r) / R, k1 = (NR * (r + 1)) / R;
+    const int b = u >> pl.scan_shift, r = u & (R - 1);
+    const int k0 = (NR * r) >> pl.scan_shift, k1 = (NR * (r + 1)) >> pl.scan_shift;
     const int w = b * 30 + lane - 1;
     // Source word of this lane for logical row k: physical row k + 1 (or N_rho - k when the
     // rows are mirrored); the zeroed guard rows supply the missing rows -1 and N_rho.
@@ -530,15 +532,16 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, in
 // ---- peak scan ----
 
 // Row range [k0, k1) of scan range r (word aligned in the packed scan).
+// (The number of ranges is a power of two, 2^scan_shift.)
 __device__ __forceinline__ void scan_rows(const Plan& pl, bool packed, int r, int& k0, int& k1) {
-  const int R = pl.scan_ranges;
+  const int sh = pl.scan_shift;
   if (packed) {
     const int W2 = pl.n_rho >> 1;
-    k0 = 2 * ((W2 * r) / R);
-    k1 = 2 * ((W2 * (r + 1)) / R);
+    k0 = 2 * ((W2 * r) >> sh);
+    k1 = 2 * ((W2 * (r + 1)) >> sh);
   } else {
-    k0 = (pl.n_rho * r) / R;
-    k1 = (pl.n_rho * (r + 1)) / R;
+    k0 = (pl.n_rho * r) >> sh;
+    k1 = (pl.n_rho * (r + 1)) >> sh;
   }
 }
 
@@ -586,7 +589,7 @@ __device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t*
   const int nblk = (wt + 29) / 30;
   const uint32_t TT = (uint32_t)pl.threshold | ((uint32_t)pl.threshold << 16);
   for (int u = warp; u < nblk * R; u += nwarps) {
-    const int b = u / R, r = u % R;
+    const int b = u >> pl.scan_shift, r = u & (R - 1);
     int k0, k1;
     scan_rows(pl, true, r, k0, k1);
     const int w0 = k0 >> 1, w1 = k1 >> 1;
@@ -656,7 +659,7 @@ __device__ void scan_scalar(const Plan& pl, const uint32_t* acc, const uint32_t*
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nblk = (wt + 29) / 30;
   for (int u = warp; u < nblk * R; u += nwarps) {
-    const int b = u / R, r = u % R;
+    const int b = u >> pl.scan_shift, r = u & (R - 1);
     int k0, k1;
     scan_rows(pl, false, r, k0, k1);
     const int c = b * 30 + lane - 1;
@@ -775,8 +778,75 @@ __device__ int select_chunk(const Plan& pl, const void* buf, int cn, long long m
   return kept;
 }
 
+// Selection over the vote's staged hits (mirror-pair plan, one chunk, no wide hits): floats
+// (u, v) in staging order with their original index. The bin comes from the vote's float
+// estimate (physical row p = k + 1 read off the bit pattern, exact integer path when
+// ambiguous); the dilated bitmaps carry guard bits 0 and N_rho + 1 equal to the edge bins'.
+__device__ __forceinline__ bool sel_test_fp(const Plan& pl, float u, float v, int d, const float2* fab,
+                                            const int2* cs, const uint32_t* bm) {
+  const float2 ab = fab[d];
+  const uint32_t y = (uint32_t)__float_as_int(__fmaf_rn(u, ab.x, __fmaf_rn(v, ab.y, pl.mp_c0)));
+  int p;
+  if ((y & (uint32_t)pl.mp_fmask) < (uint32_t)pl.mp_amb_lim) {
+    const int2 c2 = cs[d];
+    p = rho_bin32(__float2int_rn(u) * c2.x + (__float2int_rn(v) * c2.y + (int)kH), pl.magic) + 1;
+  } else {
+    p = (int)(y >> pl.mp_F) & ((int)(pl.mp_pmask >> 7));
+  }
+  return (bm[d * pl.nrb_g + (p >> 5)] >> (p & 31)) & 1u;
+}
+
+__device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx, int nv, long long a,
+                             uint8_t* __restrict__ mask, const int2* cs, const float2* fab, const uint32_t* bm, int D,
+                             uint32_t* unres) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int cap = min(D, kSelCap);
+  const float2* hf = reinterpret_cast<const float2*>(hb);
+  int kept = 0;
+  for (int i0 = 0; i0 < nv; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    bool hard = false;
+    if (i < nv) {
+      const float2 h = hf[i];
+      bool m = false;
+      for (int d = 0; d < cap && !m; ++d) m = sel_test_fp(pl, h.x, h.y, d, fab, cs, bm);
+      if (m) {
+        mask[a + idx[i]] = 1;
+        ++kept;
+      } else {
+        hard = cap < D;
+      }
+    }
+    const unsigned hbits = __ballot_sync(kFull, hard);
+    if (lane == 0) unres[(i0 >> 5) + warp] = hbits;
+  }
+  __syncthreads();
+  if (D > cap) {
+    const int nw = (nv + 31) >> 5;
+    for (int wi = warp; wi < nw; wi += nwarps) {
+      uint32_t bits = unres[wi];
+      while (bits) {
+        const int i = (wi << 5) + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float2 h = hf[i];
+        bool m = false;
+        for (int d0 = cap; d0 < D && !m; d0 += 32) {
+          const int d = d0 + lane;
+          m = __any_sync(kFull, d < D && sel_test_fp(pl, h.x, h.y, d, fab, cs, bm));
+        }
+        if (lane == 0 && m) {
+          mask[a + idx[i]] = 1;
+          ++kept;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return kept;
+}
+
 struct ItemShared {
-  int nv, flags, wide, last, total, D;
+  int nv, flags, wide, last, total, D, reuse;
   int kept_tot;
   long long tstart[64];
   int tmp[32];
@@ -786,13 +856,16 @@ struct ItemShared {
 // Back-projection of every hit of event e against its stored peaks pk[0, S).
 __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh,
                             const int16_t* tc, const int16_t* ts, long long a, int n, const hough_peak* pk, int S) {
-  const int NT = pl.n_theta, NR = pl.n_rho, nrb = pl.nrb, tid = threadIdx.x, bd = blockDim.x;
+  const int NT = pl.n_theta, NR = pl.n_rho, tid = threadIdx.x, bd = blockDim.x;
   int* colcnt = reinterpret_cast<int*>(smem + pl.off_acc);
   int* colidx = colcnt + NT;
   int* hist = colidx + NT;
   int2* cs = reinterpret_cast<int2*>(hist + 64);
-  uint32_t* bm = reinterpret_cast<uint32_t*>(cs + NT);
+  float2* fab = reinterpret_cast<float2*>(cs + NT);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(fab + NT);
   uint32_t* unres = reinterpret_cast<uint32_t*>(smem + pl.off_unres);
+  const bool staged = sh.reuse != 0;
+  const int nrb = staged ? pl.nrb_g : pl.nrb;  // guard-bit bitmaps are one bit wider on each side
   for (int i = tid; i < NT; i += bd) colcnt[i] = 0;
   for (int i = tid; i < 64; i += bd) hist[i] = 0;
   __syncthreads();
@@ -821,6 +894,7 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
       const int pos = atomicAdd(&hist[63 - min(cc, 63)], 1);
       colidx[j] = pos;
       cs[pos] = make_int2(tc[j], ts[j]);
+      fab[pos] = make_float2(__fmul_rn((float)tc[j], pl.fp_scale), __fmul_rn((float)ts[j], pl.fp_scale));
     }
   }
   __syncthreads();
@@ -831,7 +905,11 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   for (int q = tid; q < S; q += bd) {
     const hough_peak pq = pk[q];
     const int d = colidx[pq.theta_bin];
-    const int lo = max(0, (int)pq.rho_bin - hw), hi = min(NR - 1, (int)pq.rho_bin + hw);
+    int lo = max(0, (int)pq.rho_bin - hw), hi = min(NR - 1, (int)pq.rho_bin + hw);
+    if (staged) {  // bit k + 1 for row k; guard bits 0 and N_rho + 1 copy rows 0 and N_rho - 1
+      lo = (lo == 0) ? 0 : lo + 1;
+      hi = (hi == NR - 1) ? NR + 1 : hi + 1;
+    }
     for (int w = lo >> 5; w <= (hi >> 5); ++w) {
       const int b0 = max(lo, w << 5) & 31, b1 = min(hi, (w << 5) + 31) & 31;
       const uint32_t bits = (b1 == 31 ? 0xffffffffu : ((1u << (b1 + 1)) - 1u)) & ~((1u << b0) - 1u);
@@ -843,6 +921,13 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   if (D == 0) {
     for (int i = tid; i < n; i += bd) io.mask[a + i] = 0;
     return 0;
+  }
+  if (staged) {
+    for (int i = tid; i < n; i += bd) io.mask[a + i] = 0;
+    __syncthreads();
+    return select_staged(pl, reinterpret_cast<const int2*>(smem + pl.off_hits),
+                         reinterpret_cast<const uint16_t*>(smem + pl.off_idx), sh.nv, a, io.mask, cs, fab, bm, D,
+                         unres);
   }
   int2* hb = reinterpret_cast<int2*>(smem + pl.off_hits);
   longlong2* hw64 = reinterpret_cast<longlong2*>(smem + pl.off_hits);
@@ -951,6 +1036,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   }
 
   // 2. map + vote, chunk by chunk
+  if (tid == 0) sh.reuse = (pl.mp && n > 0 && n <= pl.hit_cap) ? 1 : 0;
   for (int h0 = 0; h0 < n; h0 += pl.hit_cap) {
     const int cn = min(pl.hit_cap, n - h0);
     __syncthreads();
@@ -959,10 +1045,12 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       sh.wide = 0;
     }
     __syncthreads();
-    stage_vote32(io.xy, a + h0, cn, hb, &sh.nv, &sh.wide, pl.fpbin != 0, pl.mp ? pl.mp_lsq : 0);
+    stage_vote32(io.xy, a + h0, cn, hb, &sh.nv, &sh.wide, pl.fpbin != 0, pl.mp ? pl.mp_lsq : 0,
+                 pl.mp ? reinterpret_cast<uint16_t*>(smem + pl.off_idx) : nullptr);
     __syncthreads();
-    if (sh.wide & 2) {
-      if (tid == 0) sh.flags |= HOUGH_F_BAD_HIT;
+    if (tid == 0) {
+      if (sh.wide & 2) sh.flags |= HOUGH_F_BAD_HIT;
+      if (sh.wide & 1) sh.reuse = 0;  // wide hits are not in the staged list
     }
     if (!(sh.wide & 1)) {
       if (pl.mp)
@@ -1008,7 +1096,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   const int maxp = pl.max_peaks;
   hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
   for (int key = tid; key < wt * R; key += bd) {
-    const int c = key / R, r = key % R;
+    const int c = key >> pl.scan_shift, r = key & (R - 1);
     int k0, k1;
     scan_rows(pl, packed, r, k0, k1);
     if (k0 >= k1) continue;

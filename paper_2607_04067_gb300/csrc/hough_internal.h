@@ -21,8 +21,10 @@ struct Plan {
   int acc32;      // 1: one int32 cell per shared word; 0: two int16 cells per word
   int nrho_pad;   // rows allocated per column
   int nrb;        // 32-bit bitmap words per column
+  int nrb_g;      // bitmap words per column with one guard bit on each side
   int hit_cap;    // hits staged in shared memory per chunk
-  int scan_ranges;  // row ranges of the peak scan
+  int scan_ranges;  // row ranges of the peak scan (a power of two)
+  int scan_shift;   // log2(scan_ranges)
   int grab;       // persistent queue: items per pop
   int mirror;     // 1: each vote lane owns column j and its mirror N_theta-1-j
   int fpbin;      // 1: fast-path bins from a float estimate, exact integer path when ambiguous
@@ -33,7 +35,7 @@ struct Plan {
   long long mp_lsq;  // fast path when u^2 + v^2 <= mp_lsq (rho within half a bin of the range)
   float fp_scale, fp_c0, fp_khi, fp_dlo, fp_dhi;  // N_rho/2H, N_rho/2, N_rho-1/2, delta-1/2, -delta-1/2
   // shared-memory layout in bytes
-  int off_acc, region_bytes, off_halo, off_hits, off_pbits, off_cnt, off_unres, off_trig, smem_bytes;
+  int off_acc, region_bytes, off_halo, off_hits, off_idx, off_pbits, off_cnt, off_unres, off_trig, smem_bytes;
   BinMagic magic;
 };
 
