@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--workload", default="batched", choices=sorted(gen.CONFIGS))
     ap.add_argument("--events", type=int, default=0, help="events per rank (0 = the workload's size)")
     ap.add_argument("--ref-events", type=int, default=3000, help="oracle events per reference step")
-    ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle events for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=10000, help="oracle events for cpu_baseline")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each serving stream")

@@ -180,11 +180,15 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       const int F = 23 - b;
       pl.rows_phys = p->n_rho + 2;
       pl.mp_F = F;
-      pl.mp_pmask = ((1 << b) - 1) << 7;
-      pl.mp_fmask = (1 << F) - 1;
-      pl.mp_amb_add = (int)std::ceil(p->n_rho * std::ldexp(1.0, F - 20)) + 1;
-      pl.mp_amb_lim = 2 * pl.mp_amb_add;
-      pl.mp_c0 = (float)(0.5 * p->n_rho + 1.0 + (double)(1 << b) + std::ldexp((double)pl.mp_amb_add, -F));
+      pl.mp_rmask = (1 << b) - 1;
+      // e >= the estimate's error bound in units of 2^-F; the ambiguous window [0, W) with
+      // W = 2e a power of two is tested by one mask
+      const int e_min = (int)std::ceil(p->n_rho * std::ldexp(1.0, F - 20)) + 1;
+      int W = 2;
+      while (W < 2 * e_min) W <<= 1;
+      pl.mp_amask = ((1 << F) - 1) & ~(W - 1);
+      pl.mp_k7 = (int)((uint32_t)((127 + b) << b) << 7);
+      pl.mp_c0 = (float)(0.5 * p->n_rho + 1.0 + (double)(1 << b) + std::ldexp((double)(W / 2), -F));
       const double L = (double)kH * (1.0 + 1.0 / p->n_rho) / 16385.0;
       pl.mp_lsq = (long long)std::floor(L * L);
     }

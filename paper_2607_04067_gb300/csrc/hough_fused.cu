@@ -380,19 +380,21 @@ __device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, const P
   return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
 }
 
-// Byte offset of the row of the vote whose float estimate, shifted by 1 + 2^b + e (2^b > N_rho + 1,
-// e = amb_add 2^-F), is kfp. In [2^b, 2^(b+1)) a float's low F = 23 - b bits are the fraction
-// and the bits above them the integer part, so both come straight from the bit pattern. The
-// estimate is within N_rho 2^-21 + 2^-(F+1) < e of the exact value; when the shifted fraction
-// is below 2e (the exact value within e of an integer) the exact integer path (clamped) decides,
-// otherwise the shift by e does not move the integer part.
-__device__ __forceinline__ uint32_t mp_row_off(float kfp, const Plan& pl, float uf, float vf, int c, int s) {
+// Shared address of the vote whose float row estimate, shifted by 1 + 2^b + e (2^b > N_rho + 1,
+// e = W/2 units of 2^-F, W a power of two), is kfp. In [2^b, 2^(b+1)) a float's low F = 23 - b
+// bits are the fraction and the bits above them (127 + b) 2^b + integer part, so
+// base2 + ((y >> F) << 7) with base2 = base - ((127 + b) 2^b << 7) is the row's word directly.
+// The estimate is within N_rho 2^-21 + 2^-(F+1) <= e of the exact value; when the shifted
+// fraction is below W (its bits above log2 W all zero: the exact value within e of an integer)
+// the exact integer path (clamped) decides, otherwise the shift by e does not move the integer part.
+__device__ __forceinline__ uint32_t mp_addr(float kfp, const Plan& pl, uint32_t base, uint32_t base2, float uf,
+                                            float vf, int c, int s) {
   const uint32_t y = (uint32_t)__float_as_int(kfp);
-  if ((y & (uint32_t)pl.mp_fmask) < (uint32_t)pl.mp_amb_lim) {
+  if ((y & (uint32_t)pl.mp_amask) == 0u) {
     const int u = __float2int_rn(uf), v = __float2int_rn(vf);
-    return (uint32_t)(rho_bin32(u * c + (v * s + (int)kH), pl.magic) + 1) << 7;
+    return base + ((uint32_t)(rho_bin32(u * c + (v * s + (int)kH), pl.magic) + 1) << 7);
   }
-  return (y >> (pl.mp_F - 7)) & (uint32_t)pl.mp_pmask;
+  return base2 + ((y >> pl.mp_F) << 7);
 }
 
 __device__ __forceinline__ void red_u32(uint32_t addr, uint32_t inc) {
@@ -403,23 +405,23 @@ __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, con
   const int cj = L.cj, sj = L.sj;
   const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
   const float c0 = pl.mp_c0;
-  const uint32_t base = L.col1;
+  const uint32_t base = L.col1, base2 = L.col1 - (uint32_t)pl.mp_k7;
   const float4* hb4 = reinterpret_cast<const float4*>(hb);
   const int np = nv >> 1, P = L.P;
 #pragma unroll 4
   for (int q = L.p; q < np; q += P) {
     const float4 h = hb4[q];
     const float v0 = __fmaf_rn(h.y, B, c0), v1 = __fmaf_rn(h.w, B, c0);
-    red_u32(base + mp_row_off(__fmaf_rn(h.x, A, v0), pl, h.x, h.y, cj, sj), 1u);
-    red_u32(base + mp_row_off(__fmaf_rn(-h.x, A, v0), pl, h.x, h.y, -cj, sj), 0x10000u);
-    red_u32(base + mp_row_off(__fmaf_rn(h.z, A, v1), pl, h.z, h.w, cj, sj), 1u);
-    red_u32(base + mp_row_off(__fmaf_rn(-h.z, A, v1), pl, h.z, h.w, -cj, sj), 0x10000u);
+    red_u32(mp_addr(__fmaf_rn(h.x, A, v0), pl, base, base2, h.x, h.y, cj, sj), 1u);
+    red_u32(mp_addr(__fmaf_rn(-h.x, A, v0), pl, base, base2, h.x, h.y, -cj, sj), 0x10000u);
+    red_u32(mp_addr(__fmaf_rn(h.z, A, v1), pl, base, base2, h.z, h.w, cj, sj), 1u);
+    red_u32(mp_addr(__fmaf_rn(-h.z, A, v1), pl, base, base2, h.z, h.w, -cj, sj), 0x10000u);
   }
   if ((nv & 1) && L.p == np % P) {
     const float2 h = reinterpret_cast<const float2*>(hb)[nv - 1];
     const float v0 = __fmaf_rn(h.y, B, c0);
-    red_u32(base + mp_row_off(__fmaf_rn(h.x, A, v0), pl, h.x, h.y, cj, sj), 1u);
-    red_u32(base + mp_row_off(__fmaf_rn(-h.x, A, v0), pl, h.x, h.y, -cj, sj), 0x10000u);
+    red_u32(mp_addr(__fmaf_rn(h.x, A, v0), pl, base, base2, h.x, h.y, cj, sj), 1u);
+    red_u32(mp_addr(__fmaf_rn(-h.x, A, v0), pl, base, base2, h.x, h.y, -cj, sj), 0x10000u);
   }
 }
 
@@ -787,11 +789,11 @@ __device__ __forceinline__ bool sel_test_fp(const Plan& pl, float u, float v, in
   const float2 ab = fab[d];
   const uint32_t y = (uint32_t)__float_as_int(__fmaf_rn(u, ab.x, __fmaf_rn(v, ab.y, pl.mp_c0)));
   int p;
-  if ((y & (uint32_t)pl.mp_fmask) < (uint32_t)pl.mp_amb_lim) {
+  if ((y & (uint32_t)pl.mp_amask) == 0u) {
     const int2 c2 = cs[d];
     p = rho_bin32(__float2int_rn(u) * c2.x + (__float2int_rn(v) * c2.y + (int)kH), pl.magic) + 1;
   } else {
-    p = (int)(y >> pl.mp_F) & ((int)(pl.mp_pmask >> 7));
+    p = (int)((y >> pl.mp_F) & (uint32_t)pl.mp_rmask);
   }
   return (bm[d * pl.nrb_g + (p >> 5)] >> (p & 31)) & 1u;
 }

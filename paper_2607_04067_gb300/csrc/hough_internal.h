@@ -30,8 +30,9 @@ struct Plan {
   int fpbin;      // 1: fast-path bins from a float estimate, exact integer path when ambiguous
   int mp;         // 1: mirror-pair word layout (column j low half, N_theta-1-j high half, guard rows)
   int rows_phys;  // mirror-pair layout: physical rows per column (N_rho + 2)
-  int mp_F, mp_pmask, mp_amb_add, mp_amb_lim, mp_fmask;  // bit extraction of the float row estimate
-  float mp_c0;    // N_rho/2 + 1 + 2^b
+  int mp_F, mp_rmask, mp_amask, mp_k7;  // float row estimate: fraction bits, row mask, ambiguity mask,
+                                        // exponent bits of (y >> F) << 7
+  float mp_c0;    // N_rho/2 + 1 + 2^b + W/2 2^-F
   long long mp_lsq;  // fast path when u^2 + v^2 <= mp_lsq (rho within half a bin of the range)
   float fp_scale, fp_c0, fp_khi, fp_dlo, fp_dhi;  // N_rho/2H, N_rho/2, N_rho-1/2, delta-1/2, -delta-1/2
   // shared-memory layout in bytes
