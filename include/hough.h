@@ -285,11 +285,13 @@ int hough_last_cuda_error(void);
 int hough_selftest_bin(int32_t n_rho, int64_t rho_lo, int64_t rho_hi, unsigned long long* d_mismatch,
                        void* stream);
 
-/* Checks the vote's float bin path (a float estimate of the bin, exact integer arithmetic
- * whenever an integer lies within N_rho 2^-20 of the estimate) on n_samples pseudo-random
- * (u_q, v_q, column) tuples of the int32 fast-path range against plain 64-bit floor
- * division: d_out[0] (uint64, caller-zeroed) gets the disagreements, d_out[1] the number of
- * tuples that took the exact integer path. */
+/* Checks the vote's float bin paths (a float estimate of the bin, exact integer arithmetic
+ * whenever an integer lies within the estimate's error bound of it) on n_samples
+ * pseudo-random (u_q, v_q, column) tuples of the int32 fast-path range against plain 64-bit
+ * floor division. d_out[5] (uint64, caller-zeroed): [0] disagreements of the general
+ * estimate, [1] its tuples that took the exact integer path, [2] disagreements of the
+ * mirror-pair layout's bit-pattern row (tuples with u^2 + v^2 inside its fast-path disc),
+ * [3] those that took its exact path, [4] the tuples inside the disc. */
 int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t n_samples, unsigned long long* d_out,
                          void* stream);
 

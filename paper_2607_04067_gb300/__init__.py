@@ -436,12 +436,14 @@ def selftest_bin(n_rho: int, rho_lo: int, rho_hi: int, stream=None) -> int:
 
 
 def selftest_fpbin(n_theta: int, n_rho: int, seed: int, n_samples: int, stream=None):
-    """(disagreements, exact-path fallbacks) of the vote's float bin path on random tuples."""
+    """(disagreements, exact-path fallbacks) of the vote's general float bin path, then
+    (disagreements, exact-path fallbacks, samples) of the mirror-pair bit-pattern row, on
+    random tuples."""
     torch = _torch()
-    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
     _check("hough_selftest_fpbin", load().hough_selftest_fpbin(n_theta, n_rho, seed, n_samples, _ptr(out),
                                                                _stream(stream)))
-    return int(out[0].item()), int(out[1].item())
+    return tuple(int(x) for x in out.tolist())
 
 
 def probe_smem_atomics(mode: int, ctas_per_sm: int, threads: int, smem_bytes: int, iters: int, sink, stream=None):

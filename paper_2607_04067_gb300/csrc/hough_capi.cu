@@ -89,7 +89,7 @@ static bool layout(Plan& pl) {
   pl.off_pbits = o;
   o += round16(wpad * pl.nrb * 4);
   pl.off_cnt = o;
-  o += round16(wpad * pl.scan_ranges * 4);
+  o += round16(wpad * pl.key_groups * 4);
   pl.off_unres = o;
   o += round16((pl.hit_cap + 1024) / 32 * 4);
   pl.off_trig = o;
@@ -108,6 +108,31 @@ static int check_params(const hough_params* p) {
   if (p->events_per_cta < 0 || p->events_per_cta > 1024) return HOUGH_EPARAM;
   if (p->block < 0 || p->block > 1024 || (p->block % 32) != 0) return HOUGH_EPARAM;
   return HOUGH_OK;
+}
+
+// Constants of the mirror-pair vote's float row estimate k_f + 1 + 2^b + e (k_f = u A + v B +
+// N_rho/2, 2^b > N_rho + 1, F = 23 - b fraction bits). Error bound of the estimate, in bins:
+// A = fl(c fl(N_rho/2H)) is within 2^-23 (1 + 2^-24) of c N_rho/2H relative, and |u c| N_rho/2H
+// <= (N_rho + 1)/2 for hits of the fast path (u^2 + v^2 <= lsq), so each product is off by
+// at most (N_rho + 1) 2^-24 (1 + 2^-23); each of the two fused multiply-adds rounds a value
+// in [2^b, 2^(b+1)) by at most 2^-(F+1). e (in units of 2^-F) is at least that bound and the
+// ambiguous window [0, 2e) a power of two wide.
+static void mp_consts(Plan& pl, int n_rho) {
+  int b = 0;
+  while ((1 << b) < n_rho + 2) ++b;
+  const int F = 23 - b;
+  pl.rows_phys = n_rho + 2;
+  pl.mp_F = F;
+  pl.mp_rmask = (1 << b) - 1;
+  const double E = (n_rho + 1) * std::ldexp(1.0, F - 23) * (1.0 + std::ldexp(1.0, -20)) + 1.0;
+  const int e_min = (int)std::ceil(E);
+  int W = 2;
+  while (W < 2 * e_min) W <<= 1;
+  pl.mp_amask = ((1 << F) - 1) & ~(W - 1);
+  pl.mp_k7 = (int)((uint32_t)((127 + b) << b) << 7);
+  pl.mp_c0 = (float)(0.5 * n_rho + 1.0 + (double)(1 << b) + std::ldexp((double)(W / 2), -F));
+  const double L = (double)kH * (1.0 + 1.0 / n_rho) / 16385.0;
+  pl.mp_lsq = (long long)std::floor(L * L);
 }
 
 // Launch shape for parameters p; acc32 < 0 lets the planner choose the cell width.
@@ -174,34 +199,42 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       pl.mirror = sym ? 1 : 0;
     }
     pl.mp = pl.mirror && !pl.acc32 && pl.fpbin;
-    if (pl.mp) {
-      int b = 0;
-      while ((1 << b) < p->n_rho + 2) ++b;
-      const int F = 23 - b;
-      pl.rows_phys = p->n_rho + 2;
-      pl.mp_F = F;
-      pl.mp_rmask = (1 << b) - 1;
-      // e >= the estimate's error bound in units of 2^-F; the ambiguous window [0, W) with
-      // W = 2e a power of two is tested by one mask
-      const int e_min = (int)std::ceil(p->n_rho * std::ldexp(1.0, F - 20)) + 1;
-      int W = 2;
-      while (W < 2 * e_min) W <<= 1;
-      pl.mp_amask = ((1 << F) - 1) & ~(W - 1);
-      pl.mp_k7 = (int)((uint32_t)((127 + b) << b) << 7);
-      pl.mp_c0 = (float)(0.5 * p->n_rho + 1.0 + (double)(1 << b) + std::ldexp((double)(W / 2), -F));
-      const double L = (double)kH * (1.0 + 1.0 / p->n_rho) / 16385.0;
-      pl.mp_lsq = (long long)std::floor(L * L);
+    if (pl.mp) mp_consts(pl, p->n_rho);
+    // row ranges of the peak scan: the power of two that minimises the slowest warp's row
+    // steps, each unit (30 columns x one range) paying two extra rows to prime its window
+    {
+      const bool packed = !pl.mp && !pl.acc32 && (p->n_rho & 1) == 0;
+      const int cols = pl.mp ? p->n_theta / 2 : pl.tile_w;
+      const int nblk = (cols + 29) / 30, nwarps = pl.threads / 32;
+      const int rows = packed ? p->n_rho / 2 : p->n_rho;
+      long best = -1;
+      for (int Rs = 0; (1 << Rs) <= 64 && (rows >> Rs) >= 2; ++Rs) {
+        const long R = 1L << Rs;
+        const long cost = ((nblk * R + nwarps - 1) / nwarps) * ((rows + R - 1) / R + 2);
+        if (best < 0 || cost < best) {
+          best = cost;
+          pl.scan_ranges = (int)R;
+          pl.scan_shift = Rs;
+        }
+      }
     }
-    // row ranges of the peak scan: a power of two (at most 32, at most 4096 counters) that
-    // divides N_rho, so every range has the same number of rows
-    int R = 1;
-    int Rs = 0;
-    while (R < 32 && R * 2 * pl.groups * 32 <= 4096 && p->n_rho % (R * 2) == 0) {
-      R *= 2;
-      ++Rs;
+    // keys of the peak records: (column, group of bitmap words), at most 4096 per CTA
+    {
+      int kg = 1, ks = 0;
+      while (kg < pl.nrb) {
+        kg <<= 1;
+        ++ks;
+      }
+      int gw = 1;
+      while (pl.groups * 32 * kg > 4096) {
+        kg >>= 1;
+        --ks;
+        gw <<= 1;
+      }
+      pl.key_groups = kg;
+      pl.key_shift = ks;
+      pl.key_words = gw;
     }
-    pl.scan_ranges = R;
-    pl.scan_shift = Rs;
     for (int cap = 4096; cap >= 512; cap >>= 1) {
       pl.hit_cap = cap;
       if (layout(pl)) return HOUGH_OK;
@@ -742,6 +775,7 @@ int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t 
   hough_params p{n_theta, n_rho, 1, 1, 1, 0, 0, 0};
   Plan pl;
   if (!d_out || n_samples < 0 || make_plan(&p, pl) != HOUGH_OK) return HOUGH_EINVAL;
+  mp_consts(pl, n_rho);  // the mirror-pair estimate is checked whatever layout the plan chose
   TrigTable trig;
   host_trig(n_theta, &trig);
   cudaError_t e = launch_selftest_fpbin(pl, trig, seed, n_samples, d_out, (cudaStream_t)stream);

@@ -408,14 +408,29 @@ __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, con
   const uint32_t base = L.col1, base2 = L.col1 - (uint32_t)pl.mp_k7;
   const float4* hb4 = reinterpret_cast<const float4*>(hb);
   const int np = nv >> 1, P = L.P;
+  const uint32_t am = (uint32_t)pl.mp_amask;
+  const int F = pl.mp_F;
 #pragma unroll 4
   for (int q = L.p; q < np; q += P) {
     const float4 h = hb4[q];
     const float v0 = __fmaf_rn(h.y, B, c0), v1 = __fmaf_rn(h.w, B, c0);
-    red_u32(mp_addr(__fmaf_rn(h.x, A, v0), pl, base, base2, h.x, h.y, cj, sj), 1u);
-    red_u32(mp_addr(__fmaf_rn(-h.x, A, v0), pl, base, base2, h.x, h.y, -cj, sj), 0x10000u);
-    red_u32(mp_addr(__fmaf_rn(h.z, A, v1), pl, base, base2, h.z, h.w, cj, sj), 1u);
-    red_u32(mp_addr(__fmaf_rn(-h.z, A, v1), pl, base, base2, h.z, h.w, -cj, sj), 0x10000u);
+    const float k0 = __fmaf_rn(h.x, A, v0), k1 = __fmaf_rn(-h.x, A, v0);
+    const float k2 = __fmaf_rn(h.z, A, v1), k3 = __fmaf_rn(-h.z, A, v1);
+    const uint32_t y0 = (uint32_t)__float_as_int(k0), y1 = (uint32_t)__float_as_int(k1);
+    const uint32_t y2 = (uint32_t)__float_as_int(k2), y3 = (uint32_t)__float_as_int(k3);
+    // one test for the four votes; the rare group with an estimate in the ambiguous
+    // window takes the exact path vote by vote
+    if (((y0 & am) != 0u) & ((y1 & am) != 0u) & ((y2 & am) != 0u) & ((y3 & am) != 0u)) {
+      red_u32(base2 + ((y0 >> F) << 7), 1u);
+      red_u32(base2 + ((y1 >> F) << 7), 0x10000u);
+      red_u32(base2 + ((y2 >> F) << 7), 1u);
+      red_u32(base2 + ((y3 >> F) << 7), 0x10000u);
+    } else {
+      red_u32(mp_addr(k0, pl, base, base2, h.x, h.y, cj, sj), 1u);
+      red_u32(mp_addr(k1, pl, base, base2, h.x, h.y, -cj, sj), 0x10000u);
+      red_u32(mp_addr(k2, pl, base, base2, h.z, h.w, cj, sj), 1u);
+      red_u32(mp_addr(k3, pl, base, base2, h.z, h.w, -cj, sj), 0x10000u);
+    }
   }
   if ((nv & 1) && L.p == np % P) {
     const float2 h = reinterpret_cast<const float2*>(hb)[nv - 1];
@@ -453,7 +468,7 @@ __device__ void mp_fold(const Plan& pl, uint32_t* acc) {
 // For word lane w, lane w-1 holds the left neighbour of column w and the right neighbour of
 // column N-1-w; lane w+1 the other two. Lane w = -1 supplies the theta wrap (word lane 0, rows
 // mirrored, halves swapped) and lane w = N/2 the middle (word lane N/2-1, halves swapped).
-__device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, int* cnt, bool do_cs,
+__device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, bool do_cs,
                         unsigned long long& csum) {
   const int NT = pl.n_theta, NR = pl.n_rho, R = pl.scan_ranges, half = NT >> 1, rp = pl.rows_phys;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -484,49 +499,50 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, in
     }
     const uint32_t* ptr = acc + mp_word(sw, p0, rp);  // row k0 - 1
     const bool tested = lane >= 1 && lane <= 30 && w >= 0 && w < half;
-    const bool lo_lstrict = (w != 0), hi_rstrict = (w == 0);
+    // Raster order runs over theta, then rho: the row above and the preceding column are
+    // "before" a cell (strictly below it at a peak), the rest "after" (at most equal). The
+    // preceding column of the low half (column w) is lane w-1's low half (the wrapped column
+    // N-1 when w = 0: after, not before); of the high half (column N-1-w) lane w+1's high
+    // half; lane w-1's high half follows it (except for w = 0: the wrapped column 0, before).
+    // Strictness becomes +1 on that neighbour, so a cell is a peak iff C >= max(U + 1, D,
+    // VU + addU, VD + 0x10000, T) per half; cells are at most 32767, so nothing carries.
+    const uint32_t addU = (w != 0 ? 1u : 0u) | (w == 0 ? 0x10000u : 0u);
     const int clo = w, chi = NT - 1 - w;
     uint32_t U = __byte_perm(ptr[0], 0u, sel);
     ptr += step;
     uint32_t C = __byte_perm(ptr[0], 0u, sel);
     ptr += step;
-    int n_lo = 0, n_hi = 0;
-#pragma unroll 2
-    for (int k = k0; k < k1; ++k) {
-      const uint32_t D = __byte_perm(ptr[0], 0u, sel);
-      ptr += step;
-      const uint32_t VM = vmax2(vmax2(U, C), D);
-      const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
-      const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
-      const uint32_t X = vmax2(vmax2(vmax2(U, D), vmax2(VU, VD)), TT);
-      const uint32_t Y = vmax2(X, C) ^ C;  // half is 0 where C >= every neighbour and T
-      if (tested && ((Y & 0xffffu) == 0u || (Y >> 16) == 0u)) {
-        if ((Y & 0xffffu) == 0u) {
-          const int a = C & 0xffff;
-          if (a > (int)(U & 0xffff) && (!lo_lstrict || a > (int)(VU & 0xffff))) {
-            atomicOr(&pbits[clo * pl.nrb + (k >> 5)], 1u << (k & 31));
-            ++n_lo;
-          }
+    for (int ks = k0; ks < k1;) {
+      const int ke = min(k1, (ks | 31) + 1);  // rows of one bitmap word
+      uint32_t bl = 0, bh = 0;                // peak flags, newest row in bit 0
+#pragma unroll 4
+      for (int k = ks; k < ke; ++k) {
+        const uint32_t D = __byte_perm(ptr[0], 0u, sel);
+        ptr += step;
+        const uint32_t VM = vmax2(vmax2(U, C), D);
+        const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
+        const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
+        const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VU + addU, VD + 0x10000u)), TT);
+        // half of Z has bit 15 set iff C >= X there: 0x8000 - (max(X, C) - C), no borrow
+        const uint32_t Z = 0x80008000u - vmax2(X, C) + C;
+        bh = __funnelshift_l(Z, bh, 1);
+        bl = __funnelshift_l(Z << 16, bl, 1);
+        if (do_cs && tested) {
+          const unsigned a0 = C & 0xffffu, a1 = C >> 16;
+          if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)clo * NR + k + 1);
+          if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)chi * NR + k + 1);
         }
-        if ((Y >> 16) == 0u) {
-          const int a = C >> 16;
-          if (a > (int)(U >> 16) && a > (int)(VD >> 16) && (!hi_rstrict || a > (int)(VU >> 16))) {
-            atomicOr(&pbits[chi * pl.nrb + (k >> 5)], 1u << (k & 31));
-            ++n_hi;
-          }
-        }
+        U = C;
+        C = D;
       }
-      if (do_cs && tested) {
-        const unsigned a0 = C & 0xffffu, a1 = C >> 16;
-        if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)clo * NR + k + 1);
-        if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)chi * NR + k + 1);
+      if (tested) {
+        const int sh = 32 - (ke - ks) - (ks & 31);  // row ks to bit ks & 31
+        bl = __brev(bl) >> sh;
+        bh = __brev(bh) >> sh;
+        if (bl) atomicOr(&pbits[clo * pl.nrb + (ks >> 5)], bl);
+        if (bh) atomicOr(&pbits[chi * pl.nrb + (ks >> 5)], bh);
       }
-      U = C;
-      C = D;
-    }
-    if (tested) {
-      cnt[clo * R + r] = n_lo;
-      cnt[chi * R + r] = n_hi;
+      ks = ke;
     }
   }
 }
@@ -584,7 +600,7 @@ __device__ __forceinline__ ScanSrc scan_src(int c, int wt, int T, int j0, int NT
 // Packed int16 scan (N_rho even): two rows per step, max.u16x2 for the 3-row column maxima,
 // one shuffle each way for the neighbour columns, exact tie test only for candidates.
 // Missing neighbours (rho edges, no column) read as 0, which never blocks a cell >= T >= 1.
-__device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t* halo, uint32_t* pbits, int* cnt,
+__device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t* halo, uint32_t* pbits,
                             int wt, int T, int j0, bool do_cs, unsigned long long& csum) {
   const int NT = pl.n_theta, NR = pl.n_rho, W2 = NR >> 1, R = pl.scan_ranges;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -613,49 +629,47 @@ __device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t*
     const bool tested = lane >= 1 && lane <= 30 && c >= 0 && c < wt;
     const bool lstrict = !(c == 0 && j0 == 0);
     const bool rstrict = (c == wt - 1) && (j0 + wt == NT);
+    // Both rows of a word at once: a cell is a peak iff C >= max(U + 1, D, VL (+1 when the
+    // left column precedes it), VR (+1 when the right column is the wrapped column 0), T)
+    // per half; cells are at most 32767, so nothing carries across halves.
+    const uint32_t addL = lstrict ? 0x00010001u : 0u, addR = rstrict ? 0x00010001u : 0u;
     uint32_t P = fetch(w0 - 1), C = fetch(w0);
-    int cnt_l = 0;
     const unsigned long long cell0 = (unsigned long long)(j0 + c) * NR;
-    for (int w = w0; w < w1; ++w) {
-      const uint32_t N = fetch(w + 1);
-      const uint32_t U = __funnelshift_r(P, C, 16);   // rows 2w-1, 2w
-      const uint32_t D = __funnelshift_r(C, N, 16);   // rows 2w+1, 2w+2
-      const uint32_t VM = vmax2(vmax2(U, C), D);
-      const uint32_t VL = __shfl_up_sync(kFull, VM, 1);
-      const uint32_t VR = __shfl_down_sync(kFull, VM, 1);
-      if (tested) {
-        const uint32_t X = vmax2(vmax2(vmax2(U, D), vmax2(VL, VR)), TT);
-        const uint32_t Y = vmax2(X, C) ^ C;  // half is 0 where C >= every neighbour and T
-        if ((Y & 0xffffu) == 0u || (Y >> 16) == 0u) {
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int sh = hh << 4;
-            if ((Y >> sh) & 0xffffu) continue;
-            const int av = (C >> sh) & 0xffff, up = (U >> sh) & 0xffff;
-            const int lv = (VL >> sh) & 0xffff, rv = (VR >> sh) & 0xffff;
-            if (av > up && (!lstrict || av > lv) && (!rstrict || av > rv)) {
-              const int k = 2 * w + hh;
-              atomicOr(&pbits[c * pl.nrb + (k >> 5)], 1u << (k & 31));
-              ++cnt_l;
-            }
-          }
-        }
-        if (do_cs) {
+    for (int ws = w0; ws < w1;) {
+      const int we = min(w1, (ws | 15) + 1);  // row pairs of one bitmap word
+      uint32_t bits = 0;                      // peak flags, newest row in bit 0
+      for (int w = ws; w < we; ++w) {
+        const uint32_t N = fetch(w + 1);
+        const uint32_t U = __funnelshift_r(P, C, 16);   // rows 2w-1, 2w
+        const uint32_t D = __funnelshift_r(C, N, 16);   // rows 2w+1, 2w+2
+        const uint32_t VM = vmax2(vmax2(U, C), D);
+        const uint32_t VL = __shfl_up_sync(kFull, VM, 1);
+        const uint32_t VR = __shfl_down_sync(kFull, VM, 1);
+        const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VL + addL, VR + addR)), TT);
+        const uint32_t Z = 0x80008000u - vmax2(X, C) + C;  // bit 15 of a half: C >= X there
+        bits = __funnelshift_l(Z << 16, bits, 1);          // row 2w
+        bits = __funnelshift_l(Z, bits, 1);                // row 2w + 1
+        if (do_cs && tested) {
           const unsigned a0 = C & 0xffffu, a1 = C >> 16;
           if (a0) csum += (unsigned long long)a0 * mix64(cell0 + 2 * w + 1);
           if (a1) csum += (unsigned long long)a1 * mix64(cell0 + 2 * w + 2);
         }
+        P = C;
+        C = N;
       }
-      P = C;
-      C = N;
+      if (tested) {
+        const int sh = 32 - 2 * (we - ws) - ((2 * ws) & 31);  // row 2 ws to bit (2 ws) & 31
+        bits = __brev(bits) >> sh;
+        if (bits) atomicOr(&pbits[c * pl.nrb + (ws >> 4)], bits);
+      }
+      ws = we;
     }
-    if (tested) cnt[c * R + r] = cnt_l;
   }
 }
 
 // Scalar scan for the int32-cell layout or an odd N_rho: one row per step.
 template <bool A32>
-__device__ void scan_scalar(const Plan& pl, const uint32_t* acc, const uint32_t* halo, uint32_t* pbits, int* cnt,
+__device__ void scan_scalar(const Plan& pl, const uint32_t* acc, const uint32_t* halo, uint32_t* pbits,
                             int wt, int T, int j0, bool do_cs, unsigned long long& csum) {
   const int NT = pl.n_theta, NR = pl.n_rho, nrp = pl.nrho_pad, R = pl.scan_ranges;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -676,7 +690,6 @@ __device__ void scan_scalar(const Plan& pl, const uint32_t* acc, const uint32_t*
     const bool lstrict = !(c == 0 && j0 == 0);
     const bool rstrict = (c == wt - 1) && (j0 + wt == NT);
     int vp = fetch(k0 - 1), vc = fetch(k0);
-    int cnt_l = 0;
     const unsigned long long cell0 = (unsigned long long)(j0 + c) * NR;
     for (int k = k0; k < k1; ++k) {
       const int vn = fetch(k + 1);
@@ -686,13 +699,11 @@ __device__ void scan_scalar(const Plan& pl, const uint32_t* acc, const uint32_t*
       if (tested && vc >= pl.threshold && vc > vp && vc >= vn && (lstrict ? vc > vmL : vc >= vmL) &&
           (rstrict ? vc > vmR : vc >= vmR)) {
         atomicOr(&pbits[c * pl.nrb + (k >> 5)], 1u << (k & 31));
-        ++cnt_l;
       }
       if (do_cs && tested && vc > 0) csum += (unsigned long long)vc * mix64(cell0 + k + 1);
       vp = vc;
       vc = vn;
     }
-    if (tested) cnt[c * R + r] = cnt_l;
   }
 }
 
@@ -976,7 +987,6 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   const int j0 = t * pl.tile_w;
   const int wt = min(pl.tile_w, NT - j0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x;
-  const int R = pl.scan_ranges;
   const int wpad = pl.groups * 32;
   const int rows_w = A32 ? nrp : (nrp >> 1);  // words per column
 
@@ -1033,7 +1043,6 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     if (T > 1)
       for (int i = tid; i < nrp; i += bd) halo[i] = 0u;
     for (int i = tid; i < wpad * pl.nrb; i += bd) pbits[i] = 0;
-    for (int i = tid; i < wpad * R; i += bd) cnt[i] = 0;
     if (tid == 0) sh.flags = 0;
   }
 
@@ -1085,40 +1094,42 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   if (pl.mp) {
     mp_fold(pl, acc);
     __syncthreads();
-    scan_mp(pl, acc, pbits, cnt, do_cs, csum);
+    scan_mp(pl, acc, pbits, do_cs, csum);
   } else if (packed) {
-    scan_packed(pl, acc, halo, pbits, cnt, wt, T, j0, do_cs, csum);
+    scan_packed(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
   } else {
-    scan_scalar<A32>(pl, acc, halo, pbits, cnt, wt, T, j0, do_cs, csum);
+    scan_scalar<A32>(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
   }
   __syncthreads();
 
-  // 4. raster-order positions and peak records
-  const int total = block_exscan(cnt, wt * R, sh.tmp);
+  // 4. raster-order positions and peak records: keys (column, group of key_words bitmap words)
+  // in raster order, counted from the peak bitmap
+  const int KG = pl.key_groups, G = pl.key_words, nkeys = wt * KG;
+  for (int key = tid; key < nkeys; key += bd) {
+    const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
+    int np = 0;
+    for (int w = w0; w < w1; ++w) np += __popc(pbits[c * pl.nrb + w]);
+    cnt[key] = np;
+  }
+  __syncthreads();
+  const int total = block_exscan(cnt, nkeys, sh.tmp);
   const int maxp = pl.max_peaks;
   hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
-  for (int key = tid; key < wt * R; key += bd) {
-    const int c = key >> pl.scan_shift, r = key & (R - 1);
-    int k0, k1;
-    scan_rows(pl, packed, r, k0, k1);
-    if (k0 >= k1) continue;
+  for (int key = tid; key < nkeys; key += bd) {
+    const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
     int pos = cnt[key];
-    for (int w = k0 >> 5; w <= ((k1 - 1) >> 5); ++w) {
+    for (int w = w0; w < w1 && pos < maxp; ++w) {
       uint32_t bits = pbits[c * pl.nrb + w];
-      const int lo = max(k0 - (w << 5), 0), hi = min(k1 - (w << 5), 32);
-      bits &= (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-      while (bits) {
+      while (bits && pos < maxp) {
         const int bb = __ffs(bits) - 1;
         bits &= bits - 1u;
         const int k = (w << 5) + bb;
-        if (pos < maxp) {
-          hough_peak pk;
-          pk.theta_bin = (int16_t)(j0 + c);
-          pk.rho_bin = (int16_t)k;
-          pk.votes = (int16_t)(pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp));
-          pk.flags = 0;
-          dst[pos] = pk;
-        }
+        hough_peak pk;
+        pk.theta_bin = (int16_t)(j0 + c);
+        pk.rho_bin = (int16_t)k;
+        pk.votes = (int16_t)(pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp));
+        pk.flags = 0;
+        dst[pos] = pk;
         ++pos;
       }
     }
@@ -1266,7 +1277,7 @@ __global__ void __launch_bounds__(1024) prep_kernel(const long long* off, long l
 // fallback) against plain 64-bit floor division. Counts disagreements and fallbacks.
 __global__ void selftest_fpbin_kernel(const Plan pl, const TrigTable trig, unsigned long long seed, long long n,
                                       unsigned long long* out) {
-  unsigned long long bad = 0, amb = 0;
+  unsigned long long bad = 0, amb = 0, bad_mp = 0, amb_mp = 0, n_mp = 0;
   const FpBin K{pl.fp_khi, pl.fp_dlo, pl.fp_dhi};
   const long long NR = pl.n_rho;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1284,14 +1295,35 @@ __global__ void selftest_fpbin_kernel(const Plan pl, const TrigTable trig, unsig
     const long long t = (long long)u * c + (long long)v * s + kH;
     const long long ref = t < 0 ? 0 : min(NR - 1, (t * NR) / (2 * kH));
     bad += (k != ref);
+    // mirror-pair estimate: physical row from the bit pattern (guard rows 0 and N_rho + 1
+    // stand for the clamped edge bins), exact path inside the ambiguous window
+    if ((long long)u * u + (long long)v * v <= pl.mp_lsq) {
+      ++n_mp;
+      const uint32_t y = (uint32_t)__float_as_int(__fmaf_rn(uf, A, __fmaf_rn(vf, B, pl.mp_c0)));
+      long long p;
+      if ((y & (uint32_t)pl.mp_amask) == 0u) {
+        ++amb_mp;
+        p = rho_bin32(u * c + (v * s + (int)kH), pl.magic) + 1;
+      } else {
+        p = (long long)((y >> pl.mp_F) & (uint32_t)pl.mp_rmask);
+        bad_mp += (((y >> pl.mp_F) << 7) - (uint32_t)pl.mp_k7) != ((uint32_t)p << 7);
+      }
+      bad_mp += (p < 0 || p > NR + 1 || min(max(p - 1, 0LL), NR - 1) != ref);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     bad += __shfl_down_sync(kFull, bad, o);
     amb += __shfl_down_sync(kFull, amb, o);
+    bad_mp += __shfl_down_sync(kFull, bad_mp, o);
+    amb_mp += __shfl_down_sync(kFull, amb_mp, o);
+    n_mp += __shfl_down_sync(kFull, n_mp, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (bad) atomicAdd(out, bad);
     if (amb) atomicAdd(out + 1, amb);
+    if (bad_mp) atomicAdd(out + 2, bad_mp);
+    if (amb_mp) atomicAdd(out + 3, amb_mp);
+    if (n_mp) atomicAdd(out + 4, n_mp);
   }
 }
 

@@ -25,6 +25,9 @@ struct Plan {
   int hit_cap;    // hits staged in shared memory per chunk
   int scan_ranges;  // row ranges of the peak scan (a power of two)
   int scan_shift;   // log2(scan_ranges)
+  int key_groups;   // peak-record keys per column (a power of two)
+  int key_shift;    // log2(key_groups)
+  int key_words;    // bitmap words per key
   int grab;       // persistent queue: items per pop
   int mirror;     // 1: each vote lane owns column j and its mirror N_theta-1-j
   int fpbin;      // 1: fast-path bins from a float estimate, exact integer path when ambiguous

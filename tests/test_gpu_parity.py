@@ -308,10 +308,16 @@ def test_bin_function_exhaustive(h, n_rho):
 @pytest.mark.parametrize("n_theta,n_rho", [(64, 64), (256, 256), (512, 512), (1000, 1000), (1024, 1024), (37, 63)])
 def test_float_bin_path_random_tuples(h, n_theta, n_rho):
     """The vote bins through a float estimate and falls back to integer arithmetic when an
-    integer lies within N_rho 2^-20 of it; 2e8 random tuples must all agree with exact division."""
-    bad, amb = h.selftest_fpbin(n_theta, n_rho, 12345 + n_rho, 200_000_000)
+    integer lies within the estimate's error bound of it; 2e8 random tuples must all agree
+    with exact division, for the general estimate and for the mirror-pair layout's row read
+    off the float's bit pattern (whose window is a power of two of 2^-F units, F = 23 - b)."""
+    bad, amb, bad_mp, amb_mp, n_mp = h.selftest_fpbin(n_theta, n_rho, 12345 + n_rho, 200_000_000)
     assert bad == 0
     assert 0 < amb < 200_000_000 * 4e-3  # the fallback is exercised, and rare
+    assert bad_mp == 0
+    assert n_mp > 100_000_000
+    b = (n_rho + 1).bit_length()  # 2^b >= n_rho + 2
+    assert 0 < amb_mp < n_mp * 2 * 4 * 2.0 ** -(23 - b)  # window of 4 units, twice for slack
 
 
 def test_autotuned_shape_gives_identical_results(h):
