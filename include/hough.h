@@ -132,7 +132,8 @@ size_t hough_workspace_size(const hough_params* p, int64_t n_events);
  * Outputs as in the stepwise calls; d_checksum (nullable) gets per event
  * sum over cells c = j*n_rho + k of acc[c] * splitmix64_finalizer(c + 1) mod 2^64.
  * d_ws: workspace of ws_bytes >= hough_workspace_size(p, n_events), 256-byte aligned.
- * One CTA per (event, theta tile). */
+ * d_xy and d_peaks must be 8-byte aligned (each record is written as one 8-byte store);
+ * otherwise HOUGH_EINVAL. One CTA per (event, theta tile). */
 int hough_run(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events, const hough_params* p,
               int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask, int32_t* d_nkept, uint64_t* d_checksum,
               void* d_ws, size_t ws_bytes, int32_t* d_status, void* stream);

@@ -296,7 +296,7 @@ int prepare_fused(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int
   if (n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
   if (n_events > 0 && (!d_npeaks || !d_peaks || !d_nkept)) return HOUGH_EINVAL;
   if (n_hits > 0 && (!d_xy || !d_mask)) return HOUGH_EINVAL;
-  if (((uintptr_t)d_xy & 7) || ((uintptr_t)d_ws & 255)) return HOUGH_EINVAL;
+  if (((uintptr_t)d_xy & 7) || ((uintptr_t)d_peaks & 7) || ((uintptr_t)d_ws & 255)) return HOUGH_EINVAL;
   int rc = make_plan(p, cm.pl);
   if (rc) return rc;
   if ((long long)n_events * cm.pl.tiles > 0x7fffffffLL) return HOUGH_EINVAL;

@@ -866,9 +866,24 @@ struct ItemShared {
   unsigned long long red[32];
 };
 
-// Back-projection of every hit of event e against its stored peaks pk[0, S).
+// Word W of column P's peak rows dilated by +-hw (hw < 32) and cut to [0, N_rho): bit k is
+// set iff a peak lies within hw rows of k (0 outside the column's nrb words).
+__device__ __forceinline__ uint32_t dilated_word(const uint32_t* P, int W, int nrb, int NR, int hw) {
+  if (W < 0 || W >= nrb) return 0u;
+  const uint32_t pm = W > 0 ? P[W - 1] : 0u, p0 = P[W], pp = W + 1 < nrb ? P[W + 1] : 0u;
+  uint32_t d = p0;
+  for (int s = 1; s <= hw; ++s) d |= (p0 << s) | (pm >> (32 - s)) | (p0 >> s) | (pp << (32 - s));
+  const int valid = NR - (W << 5);
+  return valid < 32 ? d & ((1u << valid) - 1u) : d;
+}
+
+// Back-projection of every hit of event e against its stored peaks pk[0, S). With
+// from_bits (one tile, every peak stored, keep_halfwidth < 32) the peak columns and the
+// dilated bitmaps come straight from the scan's peak bitmap pbits, which then holds exactly
+// the stored peaks.
 __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh,
-                            const int16_t* tc, const int16_t* ts, long long a, int n, const hough_peak* pk, int S) {
+                            const int16_t* tc, const int16_t* ts, long long a, int n, const hough_peak* pk, int S,
+                            bool from_bits) {
   const int NT = pl.n_theta, NR = pl.n_rho, tid = threadIdx.x, bd = blockDim.x;
   int* colcnt = reinterpret_cast<int*>(smem + pl.off_acc);
   int* colidx = colcnt + NT;
@@ -879,10 +894,19 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   uint32_t* unres = reinterpret_cast<uint32_t*>(smem + pl.off_unres);
   const bool staged = sh.reuse != 0;
   const int nrb = staged ? pl.nrb_g : pl.nrb;  // guard-bit bitmaps are one bit wider on each side
-  for (int i = tid; i < NT; i += bd) colcnt[i] = 0;
+  const uint32_t* pbits = reinterpret_cast<const uint32_t*>(smem + pl.off_pbits);
   for (int i = tid; i < 64; i += bd) hist[i] = 0;
-  __syncthreads();
-  for (int q = tid; q < S; q += bd) atomicAdd(&colcnt[pk[q].theta_bin], 1);
+  if (from_bits) {
+    for (int j = tid; j < NT; j += bd) {
+      int cc = 0;
+      for (int w = 0; w < pl.nrb; ++w) cc += __popc(pbits[j * pl.nrb + w]);
+      colcnt[j] = cc;
+    }
+  } else {
+    for (int i = tid; i < NT; i += bd) colcnt[i] = 0;
+    __syncthreads();
+    for (int q = tid; q < S; q += bd) atomicAdd(&colcnt[pk[q].theta_bin], 1);
+  }
   __syncthreads();
   for (int j = tid; j < NT; j += bd)
     if (colcnt[j] > 0) atomicAdd(&hist[63 - min(colcnt[j], 63)], 1);
@@ -912,9 +936,31 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   }
   __syncthreads();
   const int D = sh.D;
+  const int hw = pl.keep_hw;
+  if (from_bits) {
+    for (int j = tid; j < NT; j += bd) {
+      if (colcnt[j] == 0) continue;
+      const uint32_t* P = pbits + j * pl.nrb;
+      uint32_t* out = bm + colidx[j] * nrb;
+      if (!staged) {
+        for (int W = 0; W < nrb; ++W) out[W] = dilated_word(P, W, pl.nrb, NR, hw);
+      } else {
+        // bit k + 1 for row k; guard bits 0 and N_rho + 1 copy rows 0 and N_rho - 1
+        const uint32_t last = (dilated_word(P, (NR - 1) >> 5, pl.nrb, NR, hw) >> ((NR - 1) & 31)) & 1u;
+        uint32_t prev = 0u;
+        for (int W = 0; W < nrb; ++W) {
+          const uint32_t cur = dilated_word(P, W, pl.nrb, NR, hw);
+          uint32_t g = (cur << 1) | (prev >> 31);
+          if (W == 0) g |= cur & 1u;
+          if (W == ((NR + 1) >> 5)) g |= last << ((NR + 1) & 31);
+          out[W] = g;
+          prev = cur;
+        }
+      }
+    }
+  } else {
   for (int i = tid; i < D * nrb; i += bd) bm[i] = 0;
   __syncthreads();
-  const int hw = pl.keep_hw;
   for (int q = tid; q < S; q += bd) {
     const hough_peak pq = pk[q];
     const int d = colidx[pq.theta_bin];
@@ -928,6 +974,7 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
       const uint32_t bits = (b1 == 31 ? 0xffffffffu : ((1u << (b1 + 1)) - 1u)) & ~((1u << b0) - 1u);
       atomicOr(&bm[d * nrb + w], bits);
     }
+  }
   }
   __syncthreads();
   int kept = 0;
@@ -1115,22 +1162,55 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   const int total = block_exscan(cnt, nkeys, sh.tmp);
   const int maxp = pl.max_peaks;
   hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
-  for (int key = tid; key < nkeys; key += bd) {
-    const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
-    int pos = cnt[key];
-    for (int w = w0; w < w1 && pos < maxp; ++w) {
-      uint32_t bits = pbits[c * pl.nrb + w];
-      while (bits && pos < maxp) {
-        const int bb = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const int k = (w << 5) + bb;
-        hough_peak pk;
-        pk.theta_bin = (int16_t)(j0 + c);
-        pk.rho_bin = (int16_t)k;
-        pk.votes = (int16_t)(pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp));
-        pk.flags = 0;
-        dst[pos] = pk;
-        ++pos;
+  uint2* dst2 = reinterpret_cast<uint2*>(dst);  // records are 8-byte aligned (checked on the host)
+  const int nwarps = bd >> 5;
+  if (G == 1) {
+    // A warp takes 32 consecutive keys (one bitmap word each) and writes their peaks to
+    // consecutive positions: lane i of a pass finds the key owning position P0 + i (the last
+    // lane whose start is <= it) by a shuffle search and the bit by its rank in that word.
+    for (int kb = warp * 32; kb < nkeys; kb += nwarps * 32) {
+      const int key = kb + lane;
+      uint32_t word = 0;
+      int start = total;
+      if (key < nkeys) {
+        const int w = key & (KG - 1);
+        word = (w < pl.nrb) ? pbits[(key >> pl.key_shift) * pl.nrb + w] : 0u;
+        start = cnt[key];
+      }
+      const int P0 = __shfl_sync(kFull, start, 0);
+      const int P1 = min(__shfl_sync(kFull, start + __popc(word), 31), maxp);
+      for (int o0 = P0; o0 < P1; o0 += 32) {
+        const int o = o0 + lane;
+        int l = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+          const int sc = __shfl_sync(kFull, start, l + st);
+          if (sc <= o) l += st;
+        }
+        const int r = o - __shfl_sync(kFull, start, l);
+        const uint32_t wd = __shfl_sync(kFull, word, l);
+        if (o < P1) {
+          const int kl = kb + l, c = kl >> pl.key_shift;
+          const int k = ((kl & (KG - 1)) << 5) + (int)__fns(wd, 0u, r + 1);
+          const int votes = pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp);
+          dst2[o] = make_uint2((uint32_t)(j0 + c) | ((uint32_t)k << 16), (uint32_t)votes);
+        }
+      }
+    }
+  } else {
+    for (int key = tid; key < nkeys; key += bd) {
+      const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
+      int pos = cnt[key];
+      for (int w = w0; w < w1 && pos < maxp; ++w) {
+        uint32_t bits = pbits[c * pl.nrb + w];
+        while (bits && pos < maxp) {
+          const int bb = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int k = (w << 5) + bb;
+          const int votes = pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp);
+          dst2[pos] = make_uint2((uint32_t)(j0 + c) | ((uint32_t)k << 16), (uint32_t)votes);
+          ++pos;
+        }
       }
     }
   }
@@ -1194,7 +1274,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   if (too_large) {
     for (long long i = tid; i < nll; i += bd) io.mask[a + i] = 0;
   } else {
-    kept = select_event(pl, io, smem, sh, tc, ts, a, n, io.peaks + e * (long long)maxp, min(ev_total, maxp));
+    kept = select_event(pl, io, smem, sh, tc, ts, a, n, io.peaks + e * (long long)maxp, min(ev_total, maxp),
+                        T == 1 && ev_total <= maxp && pl.keep_hw < 32);
   }
   if (tid == 0) sh.kept_tot = 0;
   __syncthreads();

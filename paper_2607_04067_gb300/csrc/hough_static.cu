@@ -69,7 +69,7 @@ extern "C" int hough_run_batched_static(const int32_t* d_xy, int64_t n_hits, con
   if (!d_off || !d_status || n_hits < 0 || n_events < 0) return HOUGH_EINVAL;
   if (n_events > 0 && (!d_npeaks || !d_peaks || !d_nkept)) return HOUGH_EINVAL;
   if (n_hits > 0 && (!d_xy || !d_mask)) return HOUGH_EINVAL;
-  if ((uintptr_t)d_xy & 7) return HOUGH_EINVAL;
+  if (((uintptr_t)d_xy & 7) || ((uintptr_t)d_peaks & 7)) return HOUGH_EINVAL;
   Plan pl;
   int rc = make_plan(p, pl, -1);
   if (rc) return rc;

@@ -349,3 +349,13 @@ def test_host_errors(h):
     with pytest.raises(h.HoughError) as ei:
         h.run(xy, off, p, out=out)
     assert ei.value.code == h.EWORKSPACE
+    # peak records are written as 8-byte stores: a buffer 2 bytes off is refused before launch
+    out = h.alloc_outputs(4, 1, p)
+    out.peaks = torch.zeros(4 * p.max_peaks + 4, dtype=torch.int16, device="cuda")[1:]
+    for batched in (False, True):
+        with pytest.raises(h.HoughError) as ei:
+            h.run(xy, off, p, out=out, batched=batched)
+        assert ei.value.code == h.EINVAL
+    with pytest.raises(h.HoughError) as ei:
+        h.run_static(xy, off, p, out)
+    assert ei.value.code == h.EINVAL
