@@ -54,6 +54,21 @@ def dist_env():
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def shard_first_event(rank: int, events_per_rank: int) -> int:
+    """Weak scaling: rank r owns events [r n, (r + 1) n) of the workload's seeded event stream."""
+    return rank * events_per_rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's); x itself alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
 
@@ -210,7 +225,8 @@ def main():
     ap.add_argument("--workload", default="batched", choices=sorted(gen.CONFIGS))
     ap.add_argument("--events", type=int, default=0, help="events per rank (0 = the workload's size)")
     ap.add_argument("--ref-events", type=int, default=3000, help="oracle events per reference step")
-    ap.add_argument("--cpu-sample", type=int, default=10000, help="oracle events for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=10000,
+                    help="oracle events for cpu_baseline (a tenth of them for the single-thread run)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each serving stream")
@@ -239,7 +255,7 @@ def main():
         torch.cuda.synchronize()
 
     n_events = args.events or cfg.n_events
-    ev = gen.generate(cfg, n_events, first_event=rank * n_events, with_truth=(rank == 0))
+    ev = gen.generate(cfg, n_events, first_event=shard_first_event(rank, n_events), with_truth=(rank == 0))
     xy = torch.from_numpy(ev.xy).cuda()
     off = torch.from_numpy(ev.off).cuda()
     p = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks)
@@ -291,11 +307,7 @@ def main():
         kern_ms.append(b.elapsed_time(e))
     barrier()
     h.set_stage_events(None, None)
-    elapsed = t_start.elapsed_time(t_end)
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(t_start.elapsed_time(t_end), dist, "cuda")
     ms_step = elapsed / args.steps
     total_events = n_events * ws * args.steps
     value = total_events / (elapsed * 1e-3)
@@ -311,11 +323,7 @@ def main():
     for _ in range(args.e2e_steps):
         runner(xy_h, off_h, stream)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = n_events * ws * args.e2e_steps / e2e_s
     h2d = ev.xy.nbytes + ev.off.nbytes
     d2h = runner.d2h_bytes()
@@ -348,8 +356,11 @@ def main():
     if not args.no_cpu:
         threads = os.cpu_count() or 1
         v, _, n, dt = oracle_baseline(cfg, ev, args.cpu_sample, threads)
+        v1, _, n1, dt1 = oracle_baseline(cfg, ev, max(1, args.cpu_sample // 10), 1)
         cpu = {"value": v, "unit": "events/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {n} events of this batch ({dt:.1f} s wall on {threads} threads)"}
+               "sample": f"first {n} events of this batch ({dt:.1f} s wall on {threads} threads, events in parallel)",
+               "single_thread": {"value": v1, "unit": "events/s", "cores": 1,
+                                 "sample": f"first {n1} events of this batch ({dt1:.1f} s on 1 thread)"}}
 
     served = None
     if not args.no_serve:
