@@ -835,26 +835,19 @@ __device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx
   }
   __syncthreads();
   if (D > cap) {
-    // Hits still open: four per warp at a time, eight lanes (eight columns per step) each.
-    const int nw = (nv + 31) >> 5, g = lane >> 3, gl = lane & 7;
+    const int nw = (nv + 31) >> 5;
     for (int wi = warp; wi < nw; wi += nwarps) {
       uint32_t bits = unres[wi];
       while (bits) {
-        uint32_t b = bits;
-        for (int k = 0; k < g; ++k) b &= b - 1u;  // this group's hit: the g-th open one
-        const bool active = b != 0u;
-        const int i = active ? (wi << 5) + __ffs(b) - 1 : 0;
-        for (int k = 0; k < 4; ++k) bits &= bits - 1u;
+        const int i = (wi << 5) + __ffs(bits) - 1;
+        bits &= bits - 1u;
         const float2 h = hf[i];
         bool m = false;
-        for (int d0 = cap; d0 < D; d0 += 8) {
-          if (!__any_sync(kFull, active && !m)) break;
-          const int d = d0 + gl;
-          const bool t = active && !m && d < D && sel_test_fp(pl, h.x, h.y, d, fab, cs, bm);
-          const unsigned bal = __ballot_sync(kFull, t);  // every lane takes part, resolved or not
-          m = m || ((bal >> (g << 3)) & 0xffu) != 0u;
+        for (int d0 = cap; d0 < D && !m; d0 += 32) {
+          const int d = d0 + lane;
+          m = __any_sync(kFull, d < D && sel_test_fp(pl, h.x, h.y, d, fab, cs, bm));
         }
-        if (gl == 0 && active && m) {
+        if (lane == 0 && m) {
           mask[a + idx[i]] = 1;
           ++kept;
         }
