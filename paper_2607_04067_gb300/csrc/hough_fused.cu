@@ -835,21 +835,26 @@ __device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx
   }
   __syncthreads();
   if (D > cap) {
+    // Open hits come in runs (staging order follows the input), so warp w takes hit
+    // 32 j + w of every word j, sweeping 32 words per ballot: runs spread over all warps.
     const int nw = (nv + 31) >> 5;
-    for (int wi = warp; wi < nw; wi += nwarps) {
-      uint32_t bits = unres[wi];
-      while (bits) {
-        const int i = (wi << 5) + __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const float2 h = hf[i];
-        bool m = false;
-        for (int d0 = cap; d0 < D && !m; d0 += 32) {
-          const int d = d0 + lane;
-          m = __any_sync(kFull, d < D && sel_test_fp(pl, h.x, h.y, d, fab, cs, bm));
-        }
-        if (lane == 0 && m) {
-          mask[a + idx[i]] = 1;
-          ++kept;
+    for (int wi0 = 0; wi0 < nw; wi0 += 32) {
+      for (int ws = warp; ws < 32; ws += nwarps) {
+        const uint32_t word = (wi0 + lane < nw) ? unres[wi0 + lane] : 0u;
+        uint32_t bits = __ballot_sync(kFull, (word >> ws) & 1u);
+        while (bits) {
+          const int i = ((wi0 + __ffs(bits) - 1) << 5) + ws;
+          bits &= bits - 1u;
+          const float2 h = hf[i];
+          bool m = false;
+          for (int d0 = cap; d0 < D && !m; d0 += 32) {
+            const int d = d0 + lane;
+            m = __any_sync(kFull, d < D && sel_test_fp(pl, h.x, h.y, d, fab, cs, bm));
+          }
+          if (lane == 0 && m) {
+            mask[a + idx[i]] = 1;
+            ++kept;
+          }
         }
       }
     }
