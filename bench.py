@@ -216,6 +216,79 @@ def measure_serving(h, cfg, p, rates, seconds, pool_events=20000, seed=11):
     return out
 
 
+def run_sweep(args, cfg):
+    """Batch-size sweep on one GPU (the paper's runtime-versus-event-count study, Sec. 4): for
+    each batch of the workload's first n events, events/s of the batched launch (persistent
+    kernel in a CUDA graph), of the plain launch (one CTA per event) and of the stepwise path
+    with its per-stage times (accumulator through HBM), events/s of the batched launch per CTA
+    size, and the CPU oracle on the host cores. One JSON line per batch size."""
+    import torch
+    import paper_2607_04067_gb300 as h
+
+    torch.cuda.set_device(0)
+    sizes = [int(x) for x in args.sweep.split(",")]
+    full = gen.generate(cfg, max(sizes), with_truth=False)
+    base = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks)
+    stream = torch.cuda.Stream()
+    threads = os.cpu_count() or 1
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for n in sizes:
+        off_np = full.off[: n + 1]
+        xy = torch.from_numpy(full.xy[: int(off_np[-1])]).cuda()
+        off = torch.from_numpy(off_np).cuda()
+        reps = max(3, min(200, 200000 // max(n, 1)))
+        row = {"workload": cfg.name, "events": n, "hits": int(off_np[-1])}
+        out = h.alloc_outputs(xy.shape[0], n, base)
+        row["batched_events_per_s"] = n / (timed(lambda: h.run(xy, off, base, out=out, batched=True,
+                                                                stream=stream), reps) * 1e-3)
+        row["plain_events_per_s"] = n / (timed(lambda: h.run(xy, off, base, out=out, stream=stream), reps) * 1e-3)
+        per_block = {}
+        for blk in (256, 512, 1024):
+            q = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks, theta_tiles=1,
+                         block=blk, events_per_cta=1)
+            try:
+                oq = h.alloc_outputs(xy.shape[0], n, q)
+                per_block[str(blk)] = n / (timed(lambda: h.run(xy, off, q, out=oq, batched=True, stream=stream),
+                                                 reps) * 1e-3)
+            except h.HoughError:
+                per_block[str(blk)] = None
+        row["batched_events_per_s_by_block"] = per_block
+        if n <= args.sweep_stepwise_max:
+            st = h.new_status()
+            uq = torch.empty(xy.shape[0], dtype=torch.int64, device="cuda")
+            vq = torch.empty_like(uq)
+            acc = torch.empty((n, cfg.n_theta, cfg.n_rho), dtype=torch.int16, device="cuda")
+            npk, pk = h.peaks(acc, base, st, stream=stream)  # allocates the peak buffers once
+            mask = torch.empty(xy.shape[0], dtype=torch.uint8, device="cuda")
+            nk = torch.empty(n, dtype=torch.int32, device="cuda")
+            stages = {
+                "map": lambda: h.map_hits(xy, off, st, uq, vq, stream=stream),
+                "vote": lambda: h.vote(uq, vq, off, base, st, acc, stream=stream),
+                "peaks": lambda: h.peaks(acc, base, st, npk, pk, stream=stream),
+                "select": lambda: h.select(uq, vq, off, base, npk, pk, st, mask, nk, stream=stream),
+            }
+            ms = {k: timed(f, max(3, reps // 4)) for k, f in stages.items()}
+            row["stepwise_stage_ms"] = ms
+            row["stepwise_events_per_s"] = n / (sum(ms.values()) * 1e-3)
+        if n <= args.sweep_oracle_max:
+            v, _, _, _ = oracle_baseline(cfg, full, n, threads)
+            row["oracle_events_per_s"] = v
+            row["oracle_threads"] = threads
+        print(json.dumps(row), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,10 +307,15 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
     ap.add_argument("--shape", default="", help="fixed launch shape 'theta_tiles,block,events_per_cta' (profiling)")
+    ap.add_argument("--sweep", default="", help="batch-size sweep instead of the benchmark, e.g. '1,10,100,1000'")
+    ap.add_argument("--sweep-stepwise-max", type=int, default=10000, help="largest batch run through the stepwise path")
+    ap.add_argument("--sweep-oracle-max", type=int, default=10000, help="largest batch timed on the CPU oracle")
     args = ap.parse_args()
     cfg = gen.CONFIGS[args.workload]
     if args.impl == "reference":
         return run_reference(args, cfg)
+    if args.sweep:
+        return run_sweep(args, cfg)
 
     import torch
     import paper_2607_04067_gb300 as h

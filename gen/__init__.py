@@ -98,6 +98,10 @@ CONFIGS = {
                           256, 256, 16, max_peaks=4096),
     "stress": EventConfig("stress", 10000, 0x5EED0004, 0, 16, 16, 0.0, 2, 120.0, 1500.0, 0, 0.40, 0.40,
                           512, 512, 20, pt_frac=0.4, pt_a2=50.0, pt_b2=120.0, max_peaks=16384),
+    # the plain_paper events (same seed) at the paper's own discretisation, 1000 x 1000 (Sec. 2);
+    # T = 12 keeps ~93 % of the track hits of these events, close to the paper's R_s
+    "paper_1000": EventConfig("paper_1000", 1000, 0x5EED0001, 1, 2, 8, 0.0, 1, 50.0, 1500.0, 0, 0.10, 0.10,
+                              1000, 1000, 12, max_peaks=1024),
 }
 
 

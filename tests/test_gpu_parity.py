@@ -80,7 +80,8 @@ def test_stepwise_vote_tiled_large_accumulator(h):
 
 # ---------------------------------------------------------------- fused path
 
-@pytest.mark.parametrize("name,n", [("plain_small", None), ("plain_paper", None), ("batched", 400), ("stress", 24)])
+@pytest.mark.parametrize("name,n", [("plain_small", None), ("plain_paper", None), ("batched", 400), ("stress", 24),
+                                    ("paper_1000", 200)])
 @pytest.mark.parametrize("batched", [False, True])
 def test_fused_matches_oracle(h, name, n, batched):
     cfg = gen.CONFIGS[name]
@@ -121,7 +122,7 @@ def test_checksum_off_gives_same_results(h):
 
 # ---------------------------------------------------------------- full-size workloads, sampled
 
-@pytest.mark.parametrize("name,sample", [("batched", 300), ("stress", 60)])
+@pytest.mark.parametrize("name,sample", [("batched", 300), ("stress", 60), ("paper_1000", 100)])
 def test_full_size_sampled(h, name, sample):
     """Whole workload in the launch configuration the benchmark times (batched, no checksum),
     then the oracle recomputes a random sample of events one by one."""
