@@ -54,8 +54,8 @@ WsLayout ws_layout(const Plan& pl, long long n_events) {
   const long long T = pl.tiles;
   w.tickets = o;
   if (T > 1) o = align256(o + 4 * (size_t)n_events);
-  w.tile_cnt = o;
-  if (T > 1) o = align256(o + 4 * (size_t)(n_events * T));
+  w.tile_cnt = o;  // per tile: record count and low-segment count
+  if (T > 1) o = align256(o + 8 * (size_t)(n_events * T));
   w.tile_cs = o;
   if (T > 1) o = align256(o + 8 * (size_t)(n_events * T));
   w.tile_peaks = o;
@@ -74,14 +74,14 @@ static int round16(int x) { return (x + 15) & ~15; }
 static bool layout(Plan& pl) {
   const int wpad = pl.groups * 32;
   const int cell = pl.acc32 ? 4 : 2;
-  const int acc_bytes = pl.mp ? (pl.n_theta / 2) * pl.rows_phys * 4 : wpad * pl.nrho_pad * cell;
+  const int acc_bytes = pl.mp ? (pl.tile_w / 2) * pl.rows_phys * 4 : wpad * pl.nrho_pad * cell;
   const int sel_bytes = (2 * pl.n_theta + 64) * 4 + pl.n_theta * 16 + pl.n_theta * pl.nrb_g * 4;
   int o = 0;
   pl.off_acc = o;
   pl.region_bytes = round16(acc_bytes > sel_bytes ? acc_bytes : sel_bytes);
   o += pl.region_bytes;
   pl.off_halo = o;
-  if (pl.tiles > 1) o += round16(2 * pl.nrho_pad * 4);
+  if (pl.tiles > 1) o += round16(2 * (pl.mp ? pl.rows_phys : pl.nrho_pad) * 4);
   pl.off_hits = o;
   o += round16(pl.hit_cap * 8);
   pl.off_idx = o;
@@ -187,10 +187,12 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       if (p->theta_tiles) return HOUGH_EPARAM;
       continue;
     }
-    // Mirror pairs need the whole theta range in one tile, whole 64-column group pairs and
-    // a table with c[N-1-j] = -c[j], s[N-1-j] = s[j] (true for round-half-away-from-zero).
+    // Mirror pairs need whole 64-column group pairs per tile (a tile then owns words
+    // [t W/2, (t+1) W/2): columns and their mirrors), a table with c[N-1-j] = -c[j],
+    // s[N-1-j] = s[j] (true for round-half-away-from-zero), and, across tiles, the
+    // mirror-pair layout itself (int16 cells, float row estimate).
     pl.mirror = 0;
-    if (T == 1 && p->n_theta % 64 == 0) {
+    if (p->n_theta % (64 * T) == 0 && (T == 1 || (!pl.acc32 && pl.fpbin))) {
       TrigTable tt;
       host_trig(p->n_theta, &tt);
       bool sym = true;
@@ -204,7 +206,7 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
     // steps, each unit (30 columns x one range) paying two extra rows to prime its window
     {
       const bool packed = !pl.mp && !pl.acc32 && (p->n_rho & 1) == 0;
-      const int cols = pl.mp ? p->n_theta / 2 : pl.tile_w;
+      const int cols = pl.mp ? pl.tile_w / 2 : pl.tile_w;
       const int nblk = (cols + 29) / 30, nwarps = pl.threads / 32;
       const int rows = packed ? p->n_rho / 2 : p->n_rho;
       long best = -1;

@@ -373,10 +373,11 @@ __device__ __forceinline__ int mp_word(int w, int p, int rows_phys) {
   return (((w >> 5) * rows_phys + p) << 5) + (w & 31);
 }
 
-__device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, const Plan& pl) {
-  const int NT = pl.n_theta;
-  const bool hi = c >= (NT >> 1);
-  const uint32_t x = acc[mp_word(hi ? NT - 1 - c : c, k + 1, pl.rows_phys)];
+// Cell (c, k) of a mirror-pair tile of Wd words; tile-local column c < Wd is word c's low half,
+// c >= Wd word 2 Wd - 1 - c's high half.
+__device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, int Wd, const Plan& pl) {
+  const bool hi = c >= Wd;
+  const uint32_t x = acc[mp_word(hi ? 2 * Wd - 1 - c : c, k + 1, pl.rows_phys)];
   return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
 }
 
@@ -403,6 +404,17 @@ __device__ __forceinline__ void red_u32(uint32_t addr, uint32_t inc) {
 
 __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, const int2* hb, int nv) {
   const int cj = L.cj, sj = L.sj;
+  if (L.halo) {  // a halo word of a tile: columns j and N-1-j, 16 lanes, exact bins
+    if (!L.on) return;
+    const float2* hf = reinterpret_cast<const float2*>(hb);
+    for (int i = L.p; i < nv; i += L.P) {
+      const float2 h = hf[i];
+      const int u = __float2int_rn(h.x), vs = __float2int_rn(h.y) * sj + (int)kH;
+      red_u32(L.col2 + ((uint32_t)(rho_bin32(u * cj + vs, pl.magic) + 1) << 2), 1u);
+      red_u32(L.col2 + ((uint32_t)(rho_bin32(vs - u * cj, pl.magic) + 1) << 2), 0x10000u);
+    }
+    return;
+  }
   const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
   const float c0 = pl.mp_c0;
   const uint32_t base = L.col1, base2 = L.col1 - (uint32_t)pl.mp_k7;
@@ -443,6 +455,16 @@ __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, con
 __device__ __forceinline__ void vote_mp64(const Plan& pl, const VoteLane& L, const longlong2* hw, int nv) {
   const BinMagic m = pl.magic;
   const long long cj = L.cj, sj = L.sj;
+  if (L.halo) {
+    if (!L.on) return;
+    for (int i = L.p; i < nv; i += L.P) {
+      const longlong2 h = hw[i];
+      const long long vs = h.y * sj + kH, uc = h.x * cj;
+      red_u32(L.col2 + ((uint32_t)(rho_bin64(vs + uc, m) + 1) << 2), 1u);
+      red_u32(L.col2 + ((uint32_t)(rho_bin64(vs - uc, m) + 1) << 2), 0x10000u);
+    }
+    return;
+  }
   for (int q = L.p; q < nv; q += L.P) {
     const longlong2 h = hw[q];
     const long long vs = h.y * sj + kH, uc = h.x * cj;
@@ -453,9 +475,9 @@ __device__ __forceinline__ void vote_mp64(const Plan& pl, const VoteLane& L, con
 
 // Guard rows into the edge rows (both halves at once: a column holds at most 32767 votes,
 // so the packed add never carries across halves).
-__device__ void mp_fold(const Plan& pl, uint32_t* acc) {
+__device__ void mp_fold(const Plan& pl, uint32_t* acc, int n_words) {
   const int rp = pl.rows_phys, NR = pl.n_rho;
-  for (int w = threadIdx.x; w < (pl.n_theta >> 1); w += blockDim.x) {
+  for (int w = threadIdx.x; w < n_words; w += blockDim.x) {
     uint32_t* col = acc + mp_word(w, 0, rp);
     col[32] += col[0];
     col[NR << 5] += col[(NR + 1) << 5];
@@ -468,9 +490,13 @@ __device__ void mp_fold(const Plan& pl, uint32_t* acc) {
 // For word lane w, lane w-1 holds the left neighbour of column w and the right neighbour of
 // column N-1-w; lane w+1 the other two. Lane w = -1 supplies the theta wrap (word lane 0, rows
 // mirrored, halves swapped) and lane w = N/2 the middle (word lane N/2-1, halves swapped).
-__device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, bool do_cs,
-                        unsigned long long& csum) {
-  const int NT = pl.n_theta, NR = pl.n_rho, R = pl.scan_ranges, half = NT >> 1, rp = pl.rows_phys;
+// A tile owns words [aw, aw + half) (columns aw.. and their mirrors); its neighbour words
+// aw - 1 and aw + half come from the halo (two contiguous columns of rows_phys words, no
+// mirroring) unless the tile starts at word 0 (theta wrap) or ends at the middle word.
+__device__ void scan_mp(const Plan& pl, const uint32_t* acc, const uint32_t* halo, int aw, int half,
+                        uint32_t* pbits, bool do_cs, unsigned long long& csum) {
+  const int NT = pl.n_theta, NR = pl.n_rho, R = pl.scan_ranges, rp = pl.rows_phys;
+  const bool first = aw == 0, last = aw + half == (NT >> 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nblk = (half + 29) / 30;
   const uint32_t TT = (uint32_t)pl.threshold | ((uint32_t)pl.threshold << 16);
@@ -482,32 +508,41 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, bo
     // rows are mirrored); the zeroed guard rows supply the missing rows -1 and N_rho.
     int sw = w, p0 = k0, step = 32;
     unsigned sel = 0x3210u;  // byte permutation: identity, or swap of the two halves
+    const uint32_t* hcol = nullptr;
     if (w < 0) {
-      sw = 0;
-      p0 = NR - (k0 - 1);
-      step = -32;
-      sel = 0x1032u;
+      if (first) {
+        sw = 0;
+        p0 = NR - (k0 - 1);
+        step = -32;
+        sel = 0x1032u;
+      } else {
+        hcol = halo;
+      }
     } else if (w >= half) {
-      if (w == half) {
+      if (w == half && last) {
         sw = half - 1;
         sel = 0x1032u;
+      } else if (w == half) {
+        hcol = halo + rp;
       } else {
         sw = 0;  // nothing: read guard row 0 (zero) throughout
         p0 = 0;
         step = 0;
       }
     }
-    const uint32_t* ptr = acc + mp_word(sw, p0, rp);  // row k0 - 1
+    const uint32_t* ptr = hcol ? hcol + k0 : acc + mp_word(sw, p0, rp);  // row k0 - 1
+    if (hcol) step = 1;
     const bool tested = lane >= 1 && lane <= 30 && w >= 0 && w < half;
     // Raster order runs over theta, then rho: the row above and the preceding column are
     // "before" a cell (strictly below it at a peak), the rest "after" (at most equal). The
-    // preceding column of the low half (column w) is lane w-1's low half (the wrapped column
-    // N-1 when w = 0: after, not before); of the high half (column N-1-w) lane w+1's high
-    // half; lane w-1's high half follows it (except for w = 0: the wrapped column 0, before).
+    // preceding column of the low half (column aw+w) is lane w-1's low half (the wrapped
+    // column N-1 at word 0: after, not before); of the high half (column N-1-aw-w) lane w+1's
+    // high half; lane w-1's high half follows it (except at word 0: the wrapped column 0).
     // Strictness becomes +1 on that neighbour, so a cell is a peak iff C >= max(U + 1, D,
     // VU + addU, VD + 0x10000, T) per half; cells are at most 32767, so nothing carries.
-    const uint32_t addU = (w != 0 ? 1u : 0u) | (w == 0 ? 0x10000u : 0u);
-    const int clo = w, chi = NT - 1 - w;
+    const uint32_t addU = (w != 0 || !first) ? 1u : 0x10000u;
+    const int clo = w, chi = 2 * half - 1 - w;                // tile-local columns
+    const int glo = aw + w, ghi = NT - 1 - aw - w;             // event columns
     uint32_t U = __byte_perm(ptr[0], 0u, sel);
     ptr += step;
     uint32_t C = __byte_perm(ptr[0], 0u, sel);
@@ -529,8 +564,8 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, uint32_t* pbits, bo
         bl = __funnelshift_l(Z << 16, bl, 1);
         if (do_cs && tested) {
           const unsigned a0 = C & 0xffffu, a1 = C >> 16;
-          if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)clo * NR + k + 1);
-          if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)chi * NR + k + 1);
+          if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)glo * NR + k + 1);
+          if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)ghi * NR + k + 1);
         }
         U = C;
         C = D;
@@ -1041,6 +1076,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x;
   const int wpad = pl.groups * 32;
   const int rows_w = A32 ? nrp : (nrp >> 1);  // words per column
+  // mirror-pair tiles: words [aw, aw + Wd), i.e. columns [aw, aw + Wd) and their mirrors
+  const int Wd = pl.mp ? (wt >> 1) : 0, aw = t * Wd;
 
   // lane roles of the vote
   VoteLane L;
@@ -1050,7 +1087,19 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   L.cj = L.sj = 0;
   L.col1 = L.col2 = 0;
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
-  if (L.halo) {
+  if (L.halo && pl.mp) {
+    // lanes 0-15: word aw - 1, lanes 16-31: word aw + Wd (both of its columns), each lane
+    // a sixteenth of the hits; none at the theta wrap or at the middle word
+    const int hs = lane >> 4, wg = hs ? aw + Wd : aw - 1;
+    L.on = hs ? (aw + Wd < (NT >> 1)) : (aw > 0);
+    if (L.on) {
+      L.cj = tc[wg];
+      L.sj = ts[wg];
+    }
+    L.col2 = (uint32_t)__cvta_generic_to_shared(halo) + (uint32_t)(hs * pl.rows_phys) * 4u;
+    L.p = lane & 15;
+    L.P = 16;
+  } else if (L.halo) {
     const int jh = lane < 16 ? (j0 - 1 + NT) % NT : (j0 + wt) % NT;
     L.on = true;
     L.cj = tc[jh];
@@ -1065,8 +1114,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     L.P = P2;
     const int c1 = gpair * 32 + lane;
     L.on = true;
-    L.cj = tc[j0 + c1];
-    L.sj = ts[j0 + c1];
+    L.cj = tc[(pl.mp ? aw : j0) + c1];
+    L.sj = ts[(pl.mp ? aw : j0) + c1];
     if (pl.mp) {
       L.col1 = acc_s + (uint32_t)mp_word(c1, 0, pl.rows_phys) * 4u;
     } else {
@@ -1093,7 +1142,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     const int nz = pl.region_bytes >> 4;
     for (int i = tid; i < nz; i += bd) z[i] = make_uint4(0u, 0u, 0u, 0u);
     if (T > 1)
-      for (int i = tid; i < nrp; i += bd) halo[i] = 0u;
+      for (int i = tid; i < (pl.mp ? 2 * pl.rows_phys : nrp); i += bd) halo[i] = 0u;
     for (int i = tid; i < wpad * pl.nrb; i += bd) pbits[i] = 0;
     if (tid == 0) sh.flags = 0;
   }
@@ -1144,9 +1193,9 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   unsigned long long csum = 0;
   const bool packed = !pl.mp && !A32 && (NR & 1) == 0;
   if (pl.mp) {
-    mp_fold(pl, acc);
+    mp_fold(pl, acc, Wd);
     __syncthreads();
-    scan_mp(pl, acc, pbits, do_cs, csum);
+    scan_mp(pl, acc, halo, aw, Wd, pbits, do_cs, csum);
   } else if (packed) {
     scan_packed(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
   } else {
@@ -1165,6 +1214,11 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   }
   __syncthreads();
   const int total = block_exscan(cnt, nkeys, sh.tmp);
+  // peaks of the tile's low columns (mirror-pair tiles: the high columns follow them)
+  const int n_low = (pl.mp && Wd < wt) ? cnt[Wd << pl.key_shift] : total;
+  // event column of tile-local column c: mirror-pair tiles hold [aw, aw + Wd) then
+  // [N - aw - Wd, N - aw), both ascending; other tiles [j0, j0 + wt)
+  const int hi0 = NT - aw - 2 * Wd;
   const int maxp = pl.max_peaks;
   hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
   uint2* dst2 = reinterpret_cast<uint2*>(dst);  // records are 8-byte aligned (checked on the host)
@@ -1197,8 +1251,9 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
         if (o < P1) {
           const int kl = kb + l, c = kl >> pl.key_shift;
           const int k = ((kl & (KG - 1)) << 5) + (int)__fns(wd, 0u, r + 1);
-          const int votes = pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp);
-          dst2[o] = make_uint2((uint32_t)(j0 + c) | ((uint32_t)k << 16), (uint32_t)votes);
+          const int votes = pl.mp ? mp_get(acc, c, k, Wd, pl) : acc_get<A32>(acc, c, k, nrp);
+          const int col = pl.mp ? (c < Wd ? aw + c : hi0 + c) : j0 + c;
+          dst2[o] = make_uint2((uint32_t)col | ((uint32_t)k << 16), (uint32_t)votes);
         }
       }
     }
@@ -1212,8 +1267,9 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
           const int bb = __ffs(bits) - 1;
           bits &= bits - 1u;
           const int k = (w << 5) + bb;
-          const int votes = pl.mp ? mp_get(acc, c, k, pl) : acc_get<A32>(acc, c, k, nrp);
-          dst2[pos] = make_uint2((uint32_t)(j0 + c) | ((uint32_t)k << 16), (uint32_t)votes);
+          const int votes = pl.mp ? mp_get(acc, c, k, Wd, pl) : acc_get<A32>(acc, c, k, nrp);
+          const int col = pl.mp ? (c < Wd ? aw + c : hi0 + c) : j0 + c;
+          dst2[pos] = make_uint2((uint32_t)col | ((uint32_t)k << 16), (uint32_t)votes);
           ++pos;
         }
       }
@@ -1227,7 +1283,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   unsigned long long ev_cs = cs_tile;
   if (T > 1) {
     if (tid == 0) {
-      io.tile_cnt[e * T + t] = total;
+      io.tile_cnt[2 * (e * T + t)] = total;
+      io.tile_cnt[2 * (e * T + t) + 1] = n_low;
       if (do_cs) io.tile_cs[e * T + t] = cs_tile;
     }
     __threadfence();
@@ -1239,13 +1296,19 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       return;
     }
     __threadfence();
+    // Raster order of the event: the tiles' low segments in tile order, then (mirror-pair
+    // tiles) their high segments in reverse tile order. Segment s < T is tile s's records
+    // [0, lo); segment T + i is tile T-1-i's records [lo, all).
+    const int nseg = pl.mp ? 2 * T : T;
     if (tid == 0) {
       long long run = 0;
       unsigned long long csa = 0;
-      for (int tt = 0; tt < T; ++tt) {
-        sh.tstart[tt] = run;
-        run += __ldcg(io.tile_cnt + e * T + tt);
-        if (do_cs) csa += __ldcg(io.tile_cs + e * T + tt);
+      for (int sg = 0; sg < nseg; ++sg) {
+        const int tt = sg < T ? sg : 2 * T - 1 - sg;
+        const int all = __ldcg(io.tile_cnt + 2 * (e * T + tt)), lo = __ldcg(io.tile_cnt + 2 * (e * T + tt) + 1);
+        sh.tstart[sg] = run;
+        run += sg < T ? lo : all - lo;
+        if (do_cs && sg < T) csa += __ldcg(io.tile_cs + e * T + tt);
       }
       sh.total = (int)run;
       sh.red[0] = csa;
@@ -1254,11 +1317,13 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     ev_total = sh.total;
     ev_cs = sh.red[0];
     hough_peak* out = io.peaks + e * (long long)maxp;
-    for (int tt = 0; tt < T; ++tt) {
-      const long long st0 = sh.tstart[tt];
-      const int ct = __ldcg(io.tile_cnt + e * T + tt);
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int tt = sg < T ? sg : 2 * T - 1 - sg;
+      const int all = __ldcg(io.tile_cnt + 2 * (e * T + tt)), lo = __ldcg(io.tile_cnt + 2 * (e * T + tt) + 1);
+      const int from = sg < T ? 0 : lo, ct = sg < T ? lo : all - lo;
+      const long long st0 = sh.tstart[sg];
       const int ncopy = (int)max(0LL, min((long long)ct, (long long)maxp - st0));
-      const hough_peak* src = io.tile_peaks + (e * T + tt) * (long long)maxp;
+      const hough_peak* src = io.tile_peaks + (e * T + tt) * (long long)maxp + from;
       for (int i = tid; i < ncopy; i += bd) {
         const int2 v = __ldcg(reinterpret_cast<const int2*>(src) + i);
         reinterpret_cast<int2*>(out)[st0 + i] = v;

@@ -96,7 +96,8 @@ def test_fused_matches_oracle(h, name, n, batched):
 @pytest.mark.parametrize("n_theta,n_rho,tiles,block", [
     (256, 256, 2, 0), (256, 256, 4, 0), (256, 256, 8, 0), (256, 256, 1, 256), (256, 256, 1, 1024),
     (256, 256, 3, 0), (64, 64, 2, 0), (64, 64, 1, 64), (100, 63, 1, 0), (100, 63, 3, 0), (4, 4, 1, 0),
-    (1024, 1024, 0, 0), (1000, 1000, 0, 0), (37, 257, 2, 0)])
+    (1024, 1024, 0, 0), (1000, 1000, 0, 0), (37, 257, 2, 0),
+    (512, 512, 4, 0), (512, 512, 8, 0), (128, 64, 2, 0), (128, 63, 2, 0)])
 def test_shapes_and_tiles(h, n_theta, n_rho, tiles, block):
     cfg = gen.CONFIGS["plain_paper"]
     ev = gen.generate(cfg, 40)
@@ -250,7 +251,7 @@ def test_peak_overflow_keeps_first_in_raster_order(h):
     ref = oracle.run(ev.xy, ev.off, oracle.params(256, 256, 16, 1, 100), threads=THREADS)
     assert ref.status == oracle.F_PEAK_OVERFLOW
     xy, off = dev(ev)
-    for tiles in (1, 2, 4):
+    for tiles in (1, 2, 3, 4):  # 2 and 4: mirror-pair tiles (low and high segments), 3: plain tiles
         out = h.run(xy, off, h.params(256, 256, 16, 1, 100, theta_tiles=tiles), batched=True)
         assert h.status(out.status) == h.F_PEAK_OVERFLOW
         assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off)
