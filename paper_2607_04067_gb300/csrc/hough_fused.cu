@@ -404,14 +404,30 @@ __device__ __forceinline__ void red_u32(uint32_t addr, uint32_t inc) {
 
 __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, const int2* hb, int nv) {
   const int cj = L.cj, sj = L.sj;
-  if (L.halo) {  // a halo word of a tile: columns j and N-1-j, 16 lanes, exact bins
+  if (L.halo) {
+    // A halo word of a tile (columns j and N-1-j), 16 lanes: the same float row estimate as
+    // the tile's own words, into a contiguous column (4 bytes per row, guard rows folded
+    // like the accumulator's), exact bins when ambiguous.
     if (!L.on) return;
     const float2* hf = reinterpret_cast<const float2*>(hb);
+    const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
+    const float c0 = pl.mp_c0;
+    const uint32_t am = (uint32_t)pl.mp_amask, base2 = L.col2 - ((uint32_t)pl.mp_k7 >> 5);
+    const int F = pl.mp_F;
+#pragma unroll 2
     for (int i = L.p; i < nv; i += L.P) {
       const float2 h = hf[i];
-      const int u = __float2int_rn(h.x), vs = __float2int_rn(h.y) * sj + (int)kH;
-      red_u32(L.col2 + ((uint32_t)(rho_bin32(u * cj + vs, pl.magic) + 1) << 2), 1u);
-      red_u32(L.col2 + ((uint32_t)(rho_bin32(vs - u * cj, pl.magic) + 1) << 2), 0x10000u);
+      const float v0 = __fmaf_rn(h.y, B, c0);
+      const uint32_t y0 = (uint32_t)__float_as_int(__fmaf_rn(h.x, A, v0));
+      const uint32_t y1 = (uint32_t)__float_as_int(__fmaf_rn(-h.x, A, v0));
+      if (((y0 & am) != 0u) & ((y1 & am) != 0u)) {
+        red_u32(base2 + ((y0 >> F) << 2), 1u);
+        red_u32(base2 + ((y1 >> F) << 2), 0x10000u);
+      } else {
+        const int u = __float2int_rn(h.x), vs = __float2int_rn(h.y) * sj + (int)kH;
+        red_u32(L.col2 + ((uint32_t)(rho_bin32(u * cj + vs, pl.magic) + 1) << 2), 1u);
+        red_u32(L.col2 + ((uint32_t)(rho_bin32(vs - u * cj, pl.magic) + 1) << 2), 0x10000u);
+      }
     }
     return;
   }
@@ -475,7 +491,7 @@ __device__ __forceinline__ void vote_mp64(const Plan& pl, const VoteLane& L, con
 
 // Guard rows into the edge rows (both halves at once: a column holds at most 32767 votes,
 // so the packed add never carries across halves).
-__device__ void mp_fold(const Plan& pl, uint32_t* acc, int n_words) {
+__device__ void mp_fold(const Plan& pl, uint32_t* acc, int n_words, uint32_t* halo) {
   const int rp = pl.rows_phys, NR = pl.n_rho;
   for (int w = threadIdx.x; w < n_words; w += blockDim.x) {
     uint32_t* col = acc + mp_word(w, 0, rp);
@@ -483,6 +499,13 @@ __device__ void mp_fold(const Plan& pl, uint32_t* acc, int n_words) {
     col[NR << 5] += col[(NR + 1) << 5];
     col[0] = 0u;  // zero guard rows now read as "no neighbour" in the scan
     col[(NR + 1) << 5] = 0u;
+  }
+  if (halo && threadIdx.x < 2) {  // the tile's two halo words (contiguous rows)
+    uint32_t* col = halo + threadIdx.x * rp;
+    col[1] += col[0];
+    col[NR] += col[NR + 1];
+    col[0] = 0u;
+    col[NR + 1] = 0u;
   }
 }
 
@@ -1193,7 +1216,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   unsigned long long csum = 0;
   const bool packed = !pl.mp && !A32 && (NR & 1) == 0;
   if (pl.mp) {
-    mp_fold(pl, acc, Wd);
+    mp_fold(pl, acc, Wd, T > 1 ? halo : nullptr);
     __syncthreads();
     scan_mp(pl, acc, halo, aw, Wd, pbits, do_cs, csum);
   } else if (packed) {
