@@ -78,6 +78,9 @@ def _load():
             lib.or_peaks.argtypes = [i16p, P(Params), ctypes.c_void_p]
             lib.or_peaks.restype = ctypes.c_int32
             lib.or_checksum.argtypes = [i16p, ctypes.c_int32, ctypes.c_int32]
+            lib.or_circles.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+            lib.or_circles.restype = None
             lib.or_checksum.restype = ctypes.c_uint64
             lib.or_run.argtypes = [i32p, ctypes.c_int64, i64p, ctypes.c_int64, P(Params), i16p, i32p,
                                    ctypes.c_void_p, u8p, i32p, u64p, ctypes.c_int32]
@@ -132,6 +135,17 @@ def peaks(acc: np.ndarray, p: Params):
 def checksum(acc: np.ndarray) -> int:
     acc = np.ascontiguousarray(acc, dtype=np.int16)
     return int(_load().or_checksum(_p(acc, ctypes.c_int16), acc.shape[0], acc.shape[1]))
+
+
+def circles(peaks: np.ndarray, n_theta: int, n_rho: int, b_tesla: float = 1.0) -> np.ndarray:
+    """Eq. (2) circle of each peak record (PEAK_DTYPE array): float64 [n, 4] = x_c mm, y_c mm,
+    r_c mm, pT MeV/c, at the bin centres."""
+    pk = np.ascontiguousarray(peaks, dtype=PEAK_DTYPE).reshape(-1)
+    out = np.zeros((len(pk), 4), np.float64)
+    if len(pk):
+        _load().or_circles(pk.ctypes.data, len(pk), int(n_theta), int(n_rho), float(b_tesla),
+                           _p(out, ctypes.c_double))
+    return out
 
 
 @dataclass

@@ -276,3 +276,20 @@ int32_t or_run(const int32_t* xy, int64_t n_hits, const int64_t* off, int64_t n_
 }
 
 int64_t or_const_H(void) { return OR_H; }
+
+/* Step 7 (Eq. 2, circle recovery): the circle through the origin that peak (j, k) stands for,
+ * taken at the bin centres th = (j + 1/2) pi / N_theta and rho = (-1 + (2k + 1) / N_rho) * 0.01
+ * mm^-1: centre x_c = cos(th) / rho, y_c = sin(th) / rho (mm), radius r_c = 1 / |rho| (mm), and
+ * the transverse momentum pT = 0.3 * B * r_c (MeV/c for B in tesla and r_c in mm; the 0.3 of the
+ * usual pT [GeV/c] = 0.3 B [T] R [m], the convention the synthetic events are drawn with).
+ * out[4 * q + 0..3] = x_c, y_c, r_c, pT for the n stored peaks of one event. */
+void or_circles(const or_peak* pk, int32_t n, int32_t n_theta, int32_t n_rho, double b_tesla, double* out) {
+  for (int32_t q = 0; q < n; ++q) {
+    const double th = ((double)pk[q].theta_bin + 0.5) * OR_PI / (double)n_theta;
+    const double rho = (-1.0 + (2.0 * (double)pk[q].rho_bin + 1.0) / (double)n_rho) * 0.01;
+    out[4 * q + 0] = cos(th) / rho;
+    out[4 * q + 1] = sin(th) / rho;
+    out[4 * q + 2] = 1.0 / fabs(rho);
+    out[4 * q + 3] = 0.3 * b_tesla * (1.0 / fabs(rho));
+  }
+}

@@ -212,6 +212,68 @@ def test_p1_random_circles_peak_near_closed_form():
         assert dj <= 1 and abs(ak - ek) <= 1 or (dj <= 1 and abs((n - 1 - ak) - ek) <= 1 and (aj == 0 or aj == n - 1))
 
 
+# ---------------------------------------------------------------- Eq. (2) circle recovery
+
+@pytest.mark.parametrize("n_theta,n_rho,j,k", [(256, 256, 75, 153), (256, 256, 255, 60), (512, 512, 300, 100),
+                                               (1000, 1000, 777, 888), (64, 64, 10, 45)])
+def test_circle_of_the_peak_passes_through_the_hits(n_theta, n_rho, j, k):
+    """The circle that a track's peak stands for (Eq. 2 at the bin centres) must pass through
+    the track's hits (to their 1 um rounding) and through the origin."""
+    th = (j + 0.5) * math.pi / n_theta
+    rho = -0.01 + (k + 0.5) * 0.02 / n_rho
+    if abs(rho) > 0.0085:
+        pytest.skip("circle too small for the chamber")
+    hits = circle_hits(math.cos(th) / rho, math.sin(th) / rho)
+    r = oracle.run(np.array(hits, np.int32), np.array([0, len(hits)], np.int64), oracle.params(n_theta, n_rho, 2))
+    stored = r.peaks[0][: r.npeaks[0]]
+    mine = [q for q in stored if int(q["theta_bin"]) == j and int(q["rho_bin"]) == k]
+    assert len(mine) == 1
+    xc, yc, rc, pt = oracle.circles(np.array(mine), n_theta, n_rho)[0]
+    assert abs(math.hypot(xc, yc) - rc) < 1e-9 * rc                      # through the origin
+    for (x, y) in hits:                                                  # through every hit
+        assert abs(math.hypot(x / 1000.0 - xc, y / 1000.0 - yc) - rc) < 2e-3
+    assert abs(pt - 0.3 * rc) < 1e-9 * pt                                # 1 T
+
+
+def test_circles_of_random_tracks_within_one_bin():
+    """Random circles through the origin: the accumulator maximum's circle has 1/r_c within
+    1.5 rho-bins of the true curvature and its centre direction within 1.5 theta-bins."""
+    rng = random.Random(5)
+    n = 256
+    dth, drho = math.pi / n, 0.02 / n
+    checked = 0
+    for _ in range(60):
+        R = rng.uniform(130.0, 2000.0)
+        phic = rng.uniform(-math.pi, math.pi)
+        hits = circle_hits(R * math.cos(phic), R * math.sin(phic))
+        if len(hits) < 6:
+            continue
+        r = oracle.run(np.array(hits, np.int32), np.array([0, len(hits)], np.int64), oracle.params(n, n, 2),
+                       with_acc=True)
+        aj, ak = divmod(int(np.argmax(r.acc[0])), n)
+        pk = np.zeros(1, oracle.PEAK_DTYPE)
+        pk["theta_bin"], pk["rho_bin"] = aj, ak
+        xc, yc, rc, pt = oracle.circles(pk, n, n)[0]
+        assert abs(1.0 / rc - 1.0 / R) <= 1.5 * drho
+        d = math.atan2(yc, xc) - phic
+        d = (d + math.pi) % (2 * math.pi) - math.pi
+        assert abs(d) <= 1.5 * dth
+        checked += 1
+    assert checked > 30
+
+
+def test_circle_sign_convention():
+    """rho < 0 stands for the circle whose centre lies opposite the column's normal (theta + pi);
+    a bin centre at rho = 0 (odd N_rho) is the straight line, radius infinite."""
+    pk = np.zeros(3, oracle.PEAK_DTYPE)
+    pk["theta_bin"] = [0, 0, 0]
+    pk["rho_bin"] = [0, 4, 2]
+    out = oracle.circles(pk, 4, 5)
+    assert out[0][0] < 0 and out[0][1] < 0 and out[1][0] > 0 and out[1][1] > 0
+    assert np.allclose(out[0][:3], -out[1][:3] * np.array([1, 1, -1]))
+    assert math.isinf(out[2][2]) and math.isinf(out[2][3])
+
+
 # ---------------------------------------------------------------- P2 invariants
 
 def local_max_rule(acc, T):
