@@ -216,6 +216,46 @@ def measure_serving(h, cfg, p, rates, seconds, pool_events=20000, seed=11):
     return out
 
 
+PT_BINS = (50.0, 100.0, 200.0, 400.0, 800.0, 1500.0)
+
+
+def track_finding(h, cfg, out, p, first_event: int, n_sample: int, dpt_max=20.0, dphi_max=0.05):
+    """Eq. (2) circles of the stored peaks against the generator's true tracks on the first
+    n_sample events: a track is found when some peak's circle has |pT - pT_true| < dpt_max MeV/c
+    and its centre direction lies within dphi_max rad of the true one. Efficiency per pT bin, and
+    the pT and direction residuals of the closest peak of each found track."""
+    import torch
+    n = min(n_sample, out.npeaks.shape[0])
+    circ = h.circles(out.npeaks[:n], out.peaks[:n], p, 1.0).cpu().numpy()
+    npk = np.minimum(out.npeaks[:n].cpu().numpy(), p.max_peaks)
+    found = np.zeros(len(PT_BINS) - 1, np.int64)
+    total = np.zeros(len(PT_BINS) - 1, np.int64)
+    dpt, dphi = [], []
+    for e in range(n):
+        c = circ[e, : npk[e]]
+        phic = np.arctan2(c[:, 1], c[:, 0])
+        for pt, q, phi0 in gen.event_tracks(cfg, first_event + e):
+            b = int(np.searchsorted(PT_BINS, pt, side="right")) - 1
+            if b < 0 or b >= len(total):
+                continue
+            total[b] += 1
+            if not len(c):
+                continue
+            d = np.angle(np.exp(1j * (phic - (phi0 - q * np.pi / 2))))
+            ok = (np.abs(c[:, 3] - pt) < dpt_max) & (np.abs(d) < dphi_max)
+            if ok.any():
+                found[b] += 1
+                i = int(np.argmin(np.where(ok, np.abs(c[:, 3] - pt) / dpt_max + np.abs(d) / dphi_max, np.inf)))
+                dpt.append(c[i, 3] - pt)
+                dphi.append(d[i])
+    return {"events": n, "criterion": f"|dpT| < {dpt_max} MeV/c and |dphi_centre| < {dphi_max} rad",
+            "efficiency_by_pt_mev": {f"{PT_BINS[i]:.0f}-{PT_BINS[i + 1]:.0f}":
+                                     (float(found[i] / total[i]) if total[i] else None) for i in range(len(total))},
+            "tracks": int(total.sum()), "found": int(found.sum()),
+            "dpt_rms_mev": float(np.sqrt(np.mean(np.square(dpt)))) if dpt else None,
+            "dphi_rms_mrad": float(1e3 * np.sqrt(np.mean(np.square(dphi)))) if dphi else None}
+
+
 def run_sweep(args, cfg):
     """Batch-size sweep on one GPU (the paper's runtime-versus-event-count study, Sec. 4): for
     each batch of the workload's first n events, events/s of the batched launch (persistent
@@ -307,6 +347,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
     ap.add_argument("--shape", default="", help="fixed launch shape 'theta_tiles,block,events_per_cta' (profiling)")
+    ap.add_argument("--physics-events", type=int, default=2000,
+                    help="events whose peaks are matched to the true tracks (Eq. 2 circles)")
     ap.add_argument("--sweep", default="", help="batch-size sweep instead of the benchmark, e.g. '1,10,100,1000'")
     ap.add_argument("--sweep-stepwise-max", type=int, default=10000, help="largest batch run through the stepwise path")
     ap.add_argument("--sweep-oracle-max", type=int, default=10000, help="largest batch timed on the CPU oracle")
@@ -479,7 +521,8 @@ def main():
                      "hbm_frac": (ev.n_hits * 9 / (kern * 1e-3)) / (peaks_meas["hbm_gbs"] * 1e9)},
         "clocks": clocks.summary(),
         "status_flags": flags,
-        "physics": {"R_c": rc, "R_s": rs, "mean_peaks_per_event": float(out.npeaks.float().mean().item())},
+        "physics": {"R_c": rc, "R_s": rs, "mean_peaks_per_event": float(out.npeaks.float().mean().item()),
+                    "track_finding": track_finding(h, cfg, out, p, 0, args.physics_events)},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))

@@ -122,6 +122,17 @@ int hough_select(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const
                  const hough_params* p, const int32_t* d_npeaks, const hough_peak* d_peaks, uint8_t* d_mask,
                  int32_t* d_nkept, int32_t* d_status, void* stream);
 
+/* Circle recovery, Eq. (2): for each stored peak (theta_bin j, rho_bin k) of each event, the
+ * circle through the origin it stands for, at the bin centres th = (j + 1/2) pi / n_theta and
+ * rho = (-1 + (2k + 1) / n_rho) * 0.01 mm^-1 (Sec. 2): d_circles[(e * max_peaks + q) * 4 + 0..3]
+ * = x_c = cos(th) / rho, y_c = sin(th) / rho (mm), r_c = 1 / |rho| (mm) and
+ * pT = 0.3 * b_tesla * r_c (MeV/c), as float (computed in double). Only the first
+ * min(d_npeaks[e], max_peaks) records of each event are read and written; the rest of
+ * d_circles is left unchanged. A rho bin centre of 0 (odd n_rho) gives infinite radius. Uses
+ * n_theta, n_rho and max_peaks of p. Enqueued on `stream`; HOUGH_EINVAL for null pointers. */
+int hough_circles(const int32_t* d_npeaks, const hough_peak* d_peaks, int64_t n_events, const hough_params* p,
+                  double b_tesla, float* d_circles, void* stream);
+
 /* ---- fused path (the accumulator never leaves shared memory) ---- */
 
 /* Device workspace bytes that hough_run / hough_run_batched need for these parameters

@@ -92,6 +92,7 @@ def load(build: bool = True):
                 "hough_run_host": [vp, i64, vp, i64, P, vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp, vp],
                 "hough_run_batched_static": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, vp],
                 "hough_autotune": [P, vp, i64, vp, i64, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(ctypes.c_float)],
+                "hough_circles": [vp, vp, i64, P, ctypes.c_double, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -239,6 +240,20 @@ def select(uq, vq, off, p: Params, npeaks, pk, st, mask=None, nkept=None, stream
         _ptr(_dev(pk, "peaks", torch.int16)), _ptr(_dev(mask, "mask", torch.uint8)),
         _ptr(_dev(nkept, "nkept", torch.int32)), _ptr(st), _stream(stream)))
     return mask, nkept
+
+
+def circles(npeaks, peaks, p: Params, b_tesla: float = 1.0, out=None, stream=None):
+    """Eq. (2) circle of every stored peak: float32 [n_events, max_peaks, 4] = x_c mm, y_c mm,
+    r_c mm, pT MeV/c (entries past each event's stored peaks are left as they were)."""
+    torch = _torch()
+    npeaks = _dev(npeaks, "npeaks", torch.int32)
+    ne = npeaks.shape[0]
+    if out is None:
+        out = torch.zeros((ne, p.max_peaks, 4), dtype=torch.float32, device=npeaks.device)
+    _check("hough_circles", load().hough_circles(_ptr(npeaks), _ptr(_dev(peaks, "peaks", torch.int16)), ne,
+                                                 ctypes.byref(p), float(b_tesla),
+                                                 _ptr(_dev(out, "circles", torch.float32)), _stream(stream)))
+    return out
 
 
 # ---------------------------------------------------------------- fused calls

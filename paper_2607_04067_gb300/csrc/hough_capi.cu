@@ -388,6 +388,18 @@ int hough_select(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const
   return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
 }
 
+int hough_circles(const int32_t* d_npeaks, const hough_peak* d_peaks, int64_t n_events, const hough_params* p,
+                  double b_tesla, float* d_circles, void* stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (n_events < 0) return HOUGH_EINVAL;
+  if (n_events > 0 && (!d_npeaks || !d_peaks || !d_circles)) return HOUGH_EINVAL;
+  if (((uintptr_t)d_peaks & 7) || ((uintptr_t)d_circles & 15)) return HOUGH_EINVAL;
+  const cudaError_t e = launch_circles(d_npeaks, d_peaks, n_events, p->n_theta, p->n_rho, p->max_peaks, b_tesla,
+                                       d_circles, (cudaStream_t)stream);
+  return e == cudaSuccess ? HOUGH_OK : cuda_fail(e);
+}
+
 size_t hough_workspace_size(const hough_params* p, int64_t n_events) {
   Plan pl;
   if (make_plan(p, pl) != HOUGH_OK || n_events < 0) return 256;

@@ -87,6 +87,8 @@ cudaError_t launch_select(const long long* uq, const long long* vq, const long l
                           const hough_params& p, const int* npeaks, const hough_peak* peaks, uint8_t* mask,
                           int* nkept, int* status, const TrigTable& trig, cudaStream_t st);
 
+cudaError_t launch_circles(const int* npeaks, const hough_peak* peaks, long long n_events, int n_theta, int n_rho,
+                           int max_peaks, double b_tesla, float* circles, cudaStream_t st);
 cudaError_t launch_pack_peaks(const int* npeaks, const hough_peak* peaks, long long n_events, int max_peaks,
                               long long* peak_off, hough_peak* dense, cudaStream_t st);
 

@@ -274,6 +274,25 @@ __global__ void probe_kernel(int mode, int words, int iters, unsigned long long*
   if (threadIdx.x == 0) atomicAdd(sink, (unsigned long long)sm[blockIdx.x % words]);
 }
 
+// Circle of each stored peak (Eq. 2 at the bin centres), one thread per record.
+__global__ void circles_kernel(const int* __restrict__ npeaks, const hough_peak* __restrict__ peaks,
+                               long long n_events, int n_theta, int n_rho, int max_peaks, double b_tesla,
+                               float4* __restrict__ out) {
+  const long long total = n_events * (long long)max_peaks;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long e = i / max_peaks;
+    const int q = (int)(i - e * max_peaks);
+    if (q >= min(npeaks[e], max_peaks)) continue;
+    const hough_peak pk = peaks[i];
+    double sn, cs;
+    sincospi(((double)pk.theta_bin + 0.5) / (double)n_theta, &sn, &cs);
+    const double rho = (-1.0 + (2.0 * (double)pk.rho_bin + 1.0) / (double)n_rho) * 0.01;
+    const double rc = 1.0 / fabs(rho);
+    out[i] = make_float4((float)(cs / rho), (float)(sn / rho), (float)rc, (float)(0.3 * b_tesla * rc));
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_map(const int2* xy, long long n_hits, long long* uq, long long* vq, int* status, cudaStream_t st) {
@@ -314,6 +333,16 @@ cudaError_t launch_select(const long long* uq, const long long* vq, const long l
   if (n_events == 0) return cudaSuccess;
   select_kernel<<<(unsigned)n_events, 256, 0, st>>>(uq, vq, off, p.n_theta, p.n_rho, p.keep_halfwidth, p.max_peaks,
                                                     host_magic(p.n_rho), npeaks, peaks, mask, nkept, status, trig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_circles(const int* npeaks, const hough_peak* peaks, long long n_events, int n_theta, int n_rho,
+                           int max_peaks, double b_tesla, float* circles, cudaStream_t st) {
+  const long long total = n_events * (long long)max_peaks;
+  if (total == 0) return cudaSuccess;
+  const long long blocks = min((total + 255) / 256, 152LL * 16);
+  circles_kernel<<<(unsigned)blocks, 256, 0, st>>>(npeaks, peaks, n_events, n_theta, n_rho, max_peaks, b_tesla,
+                                                   reinterpret_cast<float4*>(circles));
   return cudaGetLastError();
 }
 

@@ -361,3 +361,42 @@ def test_host_errors(h):
     with pytest.raises(h.HoughError) as ei:
         h.run_static(xy, off, p, out)
     assert ei.value.code == h.EINVAL
+
+
+# ---------------------------------------------------------------- Eq. (2) circle recovery
+
+@pytest.mark.parametrize("name,n", [("plain_paper", 200), ("stress", 20), ("paper_1000", 50)])
+def test_circles_match_oracle(h, name, n):
+    """Circle of every stored peak (float32 on the GPU from double arithmetic) against the
+    oracle's float64, to float rounding; records past each event's stored peaks untouched."""
+    cfg = gen.CONFIGS[name]
+    ev = gen.generate(cfg, n)
+    xy, off = dev(ev)
+    p = cfg_params(h, cfg)
+    out = h.run(xy, off, p, batched=True)
+    circ = torch.full((n, p.max_peaks, 4), -7.0, dtype=torch.float32, device="cuda")
+    h.circles(out.npeaks, out.peaks, p, 1.0, out=circ)
+    got = to_np(circ)
+    npk = np.minimum(to_np(out.npeaks), p.max_peaks)
+    pk = to_np(out.peaks)
+    for e in range(n):
+        recs = pk[e, : npk[e]].astype(np.int16).view(oracle.PEAK_DTYPE).reshape(-1)
+        ref = oracle.circles(recs, cfg.n_theta, cfg.n_rho, 1.0)
+        np.testing.assert_allclose(got[e, : npk[e]], ref.astype(np.float32), rtol=1e-6, atol=0)
+        assert np.all(got[e, npk[e]:] == -7.0)
+
+
+def test_circles_odd_rho_and_field(h):
+    """Odd N_rho has a bin centre at rho = 0 (infinite radius); pT scales with the field."""
+    p = h.params(4, 5, 1, 1, 8)
+    pk = torch.zeros((1, 8, 4), dtype=torch.int16, device="cuda")
+    pk[0, :3, 0] = torch.tensor([0, 1, 3], dtype=torch.int16)
+    pk[0, :3, 1] = torch.tensor([0, 2, 4], dtype=torch.int16)
+    npk = torch.tensor([3], dtype=torch.int32, device="cuda")
+    got = to_np(h.circles(npk, pk, p, 1.5))[0, :3]
+    recs = to_np(pk)[0, :3].view(oracle.PEAK_DTYPE).reshape(-1)
+    ref = oracle.circles(recs, 4, 5, 1.5).astype(np.float32)
+    assert np.isinf(got[1, 2]) and np.isinf(got[1, 3]) and np.isinf(ref[1, 2])
+    fin = np.isfinite(ref)
+    np.testing.assert_allclose(got[fin], ref[fin], rtol=1e-6)
+    assert np.array_equal(np.sign(got[~fin]), np.sign(ref[~fin]))
