@@ -39,11 +39,19 @@ PEAK_DTYPE = np.dtype([("theta_bin", "<i2"), ("rho_bin", "<i2"), ("votes", "<i2"
 
 class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "n_theta", "n_rho", "threshold", "keep_halfwidth", "max_peaks", "theta_tiles", "events_per_cta", "block")]
+        "n_theta", "n_rho", "threshold", "keep_halfwidth", "max_peaks", "theta_tiles", "events_per_cta", "block",
+        "peak_mode", "rel_num", "rel_den", "nms_radius")]
 
 
-def params(n_theta, n_rho, threshold, keep_halfwidth=1, max_peaks=1024) -> Params:
-    return Params(n_theta, n_rho, threshold, keep_halfwidth, max_peaks, 0, 0, 0)
+PEAK_LOCAL_MAX, PEAK_ITERATIVE = 0, 1
+
+
+def params(n_theta, n_rho, threshold, keep_halfwidth=1, max_peaks=1024, peak_mode=PEAK_LOCAL_MAX, rel_num=0,
+           rel_den=1, nms_radius=1) -> Params:
+    """Parameters; peak_mode 1 selects the iterative finder (relative threshold rel_num/rel_den of
+    the accumulator maximum, suppression half-width nms_radius)."""
+    return Params(n_theta, n_rho, threshold, keep_halfwidth, max_peaks, 0, 0, 0, peak_mode, rel_num, rel_den,
+                  nms_radius)
 
 
 def _build() -> str:
@@ -77,6 +85,8 @@ def _load():
             lib.or_bin.restype = ctypes.c_int32
             lib.or_peaks.argtypes = [i16p, P(Params), ctypes.c_void_p]
             lib.or_peaks.restype = ctypes.c_int32
+            lib.or_peaks_iterative.argtypes = [i16p, P(Params), ctypes.c_void_p]
+            lib.or_peaks_iterative.restype = ctypes.c_int32
             lib.or_checksum.argtypes = [i16p, ctypes.c_int32, ctypes.c_int32]
             lib.or_circles.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
@@ -129,6 +139,15 @@ def peaks(acc: np.ndarray, p: Params):
     acc = np.ascontiguousarray(acc, dtype=np.int16)
     out = np.zeros(max(p.max_peaks, 1), dtype=PEAK_DTYPE)
     n = _load().or_peaks(_p(acc, ctypes.c_int16), ctypes.byref(p), out.ctypes.data)
+    return int(n), out[: min(n, p.max_peaks)]
+
+
+def peaks_iterative(acc: np.ndarray, p: Params):
+    """Iterative peaks of one accumulator [n_theta, n_rho] int16: (true count, stored records in
+    extraction order)."""
+    acc = np.ascontiguousarray(acc, dtype=np.int16)
+    out = np.zeros(max(p.max_peaks, 1), dtype=PEAK_DTYPE)
+    n = _load().or_peaks_iterative(_p(acc, ctypes.c_int16), ctypes.byref(p), out.ctypes.data)
     return int(n), out[: min(n, p.max_peaks)]
 
 

@@ -48,6 +48,8 @@
 typedef struct or_params {
   int32_t n_theta, n_rho, threshold, keep_halfwidth, max_peaks;
   int32_t theta_tiles, events_per_cta, block; /* unused by the oracle */
+  int32_t peak_mode;                          /* 0: one-pass 3x3 local maxima, 1: iterative (step 5') */
+  int32_t rel_num, rel_den, nms_radius;       /* step 5' */
 } or_params;
 
 typedef struct or_peak {
@@ -136,6 +138,62 @@ int32_t or_peaks(const int16_t* acc, const or_params* p, or_peak* out) {
   return n;
 }
 
+/* Step 5' (the paper's own peak finder, Sec. 2): a relative threshold on the accumulator's
+ * global maximum, then iterative extraction with neighbourhood suppression. A cell qualifies
+ * iff acc >= threshold and acc * rel_den >= rel_num * max(acc) (the fraction rel_num/rel_den
+ * of the maximum, compared exactly in integers). Repeatedly: the qualifying cell that is not
+ * yet suppressed with the most votes (ties: the first in raster order) becomes the next peak,
+ * and every cell within nms_radius of it in theta and in rho is suppressed, itself included.
+ * theta wraps as in step 5: column j + dj outside [0, N_theta) is column j + dj -+ N_theta with
+ * rho mirrored (k -> N_rho-1-k); rows outside [0, N_rho) are skipped. Peaks are listed in
+ * extraction order, at most max_peaks stored; returns the true count. */
+int32_t or_peaks_iterative(const int16_t* acc, const or_params* p, or_peak* out) {
+  const int32_t NT = p->n_theta, NR = p->n_rho, R = p->nms_radius;
+  const int64_t ncell = (int64_t)NT * NR;
+  uint8_t* gone = (uint8_t*)calloc((size_t)(ncell > 0 ? ncell : 1), 1);
+  int32_t amax = 0;
+  for (int64_t c = 0; c < ncell; ++c)
+    if (acc[c] > amax) amax = acc[c];
+  int32_t n = 0;
+  for (;;) {
+    int64_t best = -1;
+    int32_t bv = 0;
+    for (int64_t c = 0; c < ncell; ++c) {
+      const int32_t a = acc[c];
+      if (gone[c] || a < p->threshold || (int64_t)a * p->rel_den < (int64_t)p->rel_num * amax) continue;
+      if (best < 0 || a > bv) {
+        best = c;
+        bv = a;
+      }
+    }
+    if (best < 0) break;
+    const int32_t j = (int32_t)(best / NR), k = (int32_t)(best % NR);
+    if (n < p->max_peaks) {
+      out[n].theta_bin = (int16_t)j;
+      out[n].rho_bin = (int16_t)k;
+      out[n].votes = (int16_t)bv;
+      out[n].flags = 0;
+    }
+    ++n;
+    for (int32_t dj = -R; dj <= R; ++dj) {
+      for (int32_t dk = -R; dk <= R; ++dk) {
+        int32_t jj = j + dj, kk = k + dk;
+        if (kk < 0 || kk >= NR) continue;
+        if (jj < 0) {
+          jj += NT;
+          kk = NR - 1 - kk;
+        } else if (jj >= NT) {
+          jj -= NT;
+          kk = NR - 1 - kk;
+        }
+        gone[(int64_t)jj * NR + kk] = 1;
+      }
+    }
+  }
+  free(gone);
+  return n;
+}
+
 static uint64_t or_mix64(uint64_t z) { /* SplitMix64 finaliser (Steele, Lea, Flood 2014) */
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
@@ -181,7 +239,7 @@ int32_t or_event(const int32_t* xy, int64_t n, const or_params* p, int16_t* acc,
     }
   }
   if (checksum) *checksum = or_checksum(acc, NT, NR);
-  int32_t np = or_peaks(acc, p, peaks);
+  int32_t np = p->peak_mode == 1 ? or_peaks_iterative(acc, p, peaks) : or_peaks(acc, p, peaks);
   *npeaks = np;
   if (np > p->max_peaks) status |= OR_F_PEAK_OVERFLOW;
   int32_t stored = np < p->max_peaks ? np : p->max_peaks;

@@ -493,3 +493,102 @@ def test_metrics_eq8_eq9():
     rc, rs = oracle.metrics(mask, truth)
     assert rc == pytest.approx(3 / 5)  # N_select / N_total
     assert rs == pytest.approx(2 / 3)  # N_true,select / N_true
+
+
+# ---------------------------------------------------------------- iterative peak finder (Sec. 2)
+
+def _in_window(a, b, R, NT, NR):
+    """Is cell b within the suppression window of cell a (theta wrap with mirrored rho)?"""
+    (ja, ka), (jb, kb) = a, b
+    for dj in range(-R, R + 1):
+        jj = ja + dj
+        mirrored = jj < 0 or jj >= NT
+        jj %= NT
+        if jj != jb:
+            continue
+        for dk in range(-R, R + 1):
+            kk = ka + dk
+            if kk < 0 or kk >= NR:
+                continue
+            if (NR - 1 - kk if mirrored else kk) == kb:
+                return True
+    return False
+
+
+def _greedy_peaks(acc, T, num, den, R):
+    """Independent restatement: candidates sorted by (votes desc, raster asc), each accepted
+    unless it lies in the window of an accepted one."""
+    NT, NR = acc.shape
+    amax = int(acc.max()) if acc.size else 0
+    cand = [(-int(acc[j, k]), j * NR + k) for j in range(NT) for k in range(NR)
+            if acc[j, k] >= T and int(acc[j, k]) * den >= num * amax]
+    out = []
+    for negv, c in sorted(cand):
+        cell = divmod(c, NR)
+        if not any(_in_window(p, cell, R, NT, NR) for p, _ in out):
+            out.append((cell, -negv))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_iterative_matches_greedy_restatement(seed):
+    rng = np.random.default_rng(seed)
+    NT, NR = int(rng.choice([4, 6, 8, 9])), int(rng.choice([4, 5, 8, 11]))
+    acc = rng.integers(0, 9, size=(NT, NR)).astype(np.int16)
+    T, num, den, R = int(rng.integers(1, 4)), int(rng.integers(0, 3)), 4, int(rng.integers(0, 3))
+    p = oracle.params(NT, NR, T, 1, 1000, peak_mode=oracle.PEAK_ITERATIVE, rel_num=num, rel_den=den, nms_radius=R)
+    n, pk = oracle.peaks_iterative(acc, p)
+    exp = _greedy_peaks(acc, T, num, den, R)
+    assert n == len(exp)
+    assert [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk] == exp
+
+
+def test_iterative_hand_cases():
+    NT, NR = 8, 8
+    acc = np.zeros((NT, NR), np.int16)
+    acc[2, 3] = 20      # the maximum
+    acc[3, 4] = 19      # its diagonal neighbour: suppressed with R = 1, extracted with R = 0
+    acc[6, 1] = 10      # exactly half the maximum: qualifies at 1/2 (10 * 2 >= 1 * 20)
+    acc[5, 6] = 9       # below half
+    acc[0, 0] = 15      # column 0 ...
+    acc[7, 6] = 15      # ... its wrapped neighbour (column -1 = 7, row 8-1-(0+1) = 6): tie, follows
+    p = lambda R, num, den, mx=100: oracle.params(NT, NR, 1, 1, mx, peak_mode=1, rel_num=num, rel_den=den,
+                                                 nms_radius=R)
+    n, pk = oracle.peaks_iterative(acc, p(1, 1, 2))
+    got = [(int(q["theta_bin"]), int(q["rho_bin"]), int(q["votes"])) for q in pk]
+    assert got == [(2, 3, 20), (0, 0, 15), (6, 1, 10)]
+    n, pk = oracle.peaks_iterative(acc, p(0, 1, 2))
+    got = [(int(q["theta_bin"]), int(q["rho_bin"]), int(q["votes"])) for q in pk]
+    assert got == [(2, 3, 20), (3, 4, 19), (0, 0, 15), (7, 6, 15), (6, 1, 10)]
+    n, pk = oracle.peaks_iterative(acc, p(1, 0, 1))       # no relative cut: the 9 is found too
+    assert n == 4 and int(pk[-1]["votes"]) == 9
+    n, pk = oracle.peaks_iterative(acc, p(0, 1, 2, mx=2))  # overflow: the true count, two stored
+    assert n == 5 and len(pk) == 2
+
+
+def test_iterative_invariants_on_events():
+    """On real events: every peak qualifies, no peak lies in another's window, and every
+    qualifying cell lies in the window of a peak extracted before it would have been."""
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 6)
+    NT = NR = 64
+    p = oracle.params(NT, NR, 6, 1, 4096, peak_mode=1, rel_num=1, rel_den=3, nms_radius=2)
+    r = oracle.run(ev.xy, ev.off, p, with_acc=True)
+    for e in range(ev.n_events):
+        acc = r.acc[e].astype(np.int64)
+        amax = int(acc.max())
+        peaks = [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in r.peaks[e][: r.npeaks[e]]]
+        assert len(peaks) == r.npeaks[e] > 0
+        for (c, v) in peaks:
+            assert v == acc[c] and v >= 6 and 3 * v >= amax
+        for a in range(len(peaks)):
+            for b in range(len(peaks)):
+                if a != b:
+                    assert not _in_window(peaks[a][0], peaks[b][0], 2, NT, NR)
+        order = {c: (-v, c[0] * NR + c[1]) for c, v in peaks}
+        for j in range(NT):
+            for k in range(NR):
+                v = int(acc[j, k])
+                if v < 6 or 3 * v < amax or (j, k) in order:
+                    continue
+                assert any(_in_window(c, (j, k), 2, NT, NR) and order[c] < (-v, j * NR + k) for c, _ in peaks)
