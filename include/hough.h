@@ -89,7 +89,23 @@ typedef struct hough_params {
   int32_t theta_tiles;    /* theta tiles per event (0 = auto); each tile is one CTA */
   int32_t events_per_cta; /* persistent queue: work items taken per pop (0 = auto) */
   int32_t block;          /* threads per CTA (0 = auto) */
+  /* Peak finder (Sec. 2). HOUGH_PEAK_LOCAL_MAX (0, the default): one pass of 3x3 local maxima
+   * >= threshold, listed in raster order. HOUGH_PEAK_ITERATIVE (1): the paper's own finder. A
+   * cell qualifies iff acc >= threshold and acc * rel_den >= rel_num * max(acc) (a fraction of
+   * the accumulator's maximum, exact in integers). The qualifying cell with the most votes
+   * that is not yet suppressed (ties: the first in raster order) becomes the next peak, and
+   * every cell within nms_radius of it in theta and rho is suppressed. Theta wraps with rho
+   * mirrored, and rows beyond the rho edges are skipped. Peaks are listed in extraction order.
+   * The iterative finder needs the whole accumulator in one CTA on the fused paths
+   * (theta_tiles 1); the stepwise hough_peaks takes any size. */
+  int32_t peak_mode;
+  int32_t rel_num;        /* mode 1: numerator of the relative threshold, 0 <= rel_num <= rel_den */
+  int32_t rel_den;        /* mode 1: denominator, >= 1 */
+  int32_t nms_radius;     /* mode 1: suppression half-width in bins, 0 <= 2 nms_radius < n_theta, <= 64 */
 } hough_params;
+
+#define HOUGH_PEAK_LOCAL_MAX 0
+#define HOUGH_PEAK_ITERATIVE 1
 
 /* One peak: theta bin j, rho bin k, votes acc[j][k], flags (reserved, 0). 8 bytes. */
 typedef struct hough_peak {

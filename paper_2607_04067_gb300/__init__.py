@@ -37,7 +37,8 @@ class HoughError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "n_theta", "n_rho", "threshold", "keep_halfwidth", "max_peaks", "theta_tiles", "events_per_cta", "block")]
+        "n_theta", "n_rho", "threshold", "keep_halfwidth", "max_peaks", "theta_tiles", "events_per_cta", "block",
+        "peak_mode", "rel_num", "rel_den", "nms_radius")]
 
     def __repr__(self):
         return "Params(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
@@ -55,9 +56,16 @@ class ServeResult(ctypes.Structure):
                 ("t_done_ns", ctypes.c_int64)]
 
 
+PEAK_LOCAL_MAX, PEAK_ITERATIVE = 0, 1
+
+
 def params(n_theta: int, n_rho: int, threshold: int, keep_halfwidth: int = 1, max_peaks: int = 1024,
-           theta_tiles: int = 0, events_per_cta: int = 0, block: int = 0) -> Params:
-    return Params(n_theta, n_rho, threshold, keep_halfwidth, max_peaks, theta_tiles, events_per_cta, block)
+           theta_tiles: int = 0, events_per_cta: int = 0, block: int = 0, peak_mode: int = PEAK_LOCAL_MAX,
+           rel_num: int = 0, rel_den: int = 1, nms_radius: int = 1) -> Params:
+    """Parameters of the path; peak_mode PEAK_ITERATIVE selects the paper's iterative finder
+    (relative threshold rel_num/rel_den of the maximum, suppression half-width nms_radius)."""
+    return Params(n_theta, n_rho, threshold, keep_halfwidth, max_peaks, theta_tiles, events_per_cta, block,
+                  peak_mode, rel_num, rel_den, nms_radius)
 
 
 def declared_symbols() -> list[str]:

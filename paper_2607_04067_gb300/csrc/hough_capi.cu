@@ -107,6 +107,11 @@ static int check_params(const hough_params* p) {
   if (p->theta_tiles < 0 || p->theta_tiles > 64 || p->theta_tiles > p->n_theta) return HOUGH_EPARAM;
   if (p->events_per_cta < 0 || p->events_per_cta > 1024) return HOUGH_EPARAM;
   if (p->block < 0 || p->block > 1024 || (p->block % 32) != 0) return HOUGH_EPARAM;
+  if (p->peak_mode != HOUGH_PEAK_LOCAL_MAX && p->peak_mode != HOUGH_PEAK_ITERATIVE) return HOUGH_EPARAM;
+  if (p->peak_mode == HOUGH_PEAK_ITERATIVE &&
+      (p->rel_den < 1 || p->rel_num < 0 || p->rel_num > p->rel_den || p->nms_radius < 0 || p->nms_radius > 64 ||
+       2 * p->nms_radius >= p->n_theta))
+    return HOUGH_EPARAM;
   return HOUGH_OK;
 }
 
@@ -145,6 +150,10 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
   pl.threshold = p->threshold;
   pl.keep_hw = p->keep_halfwidth;
   pl.max_peaks = p->max_peaks;
+  pl.peak_mode = p->peak_mode;
+  pl.rel_num = p->rel_num;
+  pl.rel_den = p->rel_den;
+  pl.nms_radius = p->nms_radius;
   pl.nrb = (p->n_rho + 31) / 32;
   pl.nrb_g = (p->n_rho + 2 + 31) / 32;
   pl.magic = host_magic(p->n_rho);
@@ -160,6 +169,10 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
   }
   const int cell_choice = acc32 < 0 ? 0 : acc32;
   for (int T = (p->theta_tiles ? p->theta_tiles : 1); T <= (p->theta_tiles ? p->theta_tiles : 64); ++T) {
+    if (p->peak_mode == HOUGH_PEAK_ITERATIVE && T > 1) {
+      if (p->theta_tiles) return HOUGH_EPARAM;  // the iterative finder needs the whole accumulator
+      break;
+    }
     const int W = (p->n_theta + T - 1) / T;
     if ((T - 1) * W >= p->n_theta) continue;  // every tile must own at least one column
     pl.tiles = T;

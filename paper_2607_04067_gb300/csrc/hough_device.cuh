@@ -99,6 +99,100 @@ __device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
+// Iterative peak extraction (the paper's finder, Sec. 2) over an accumulator behind `cells`
+// (get(j, k) -> votes of a cell not yet suppressed, 0 once suppressed; clear(j, k) suppresses).
+// cm: n_theta words of shared scratch holding each column's best cell packed as
+// (votes << 16) | (n_rho - 1 - k), so that the larger word is the cell with more votes and, on
+// equal votes, the smaller k. The whole CTA fills cm; warp 0 then extracts: the column word
+// with the most votes (equal votes: the smaller column) is the next peak if it qualifies, its window is
+// cleared and the 2R + 1 columns it touches are re-scanned. Every pass clears the extracted
+// cell, so the loop ends. Records go to dst in extraction order (the first max_peaks);
+// returns the true count (valid in every thread).
+template <class Cells>
+__device__ int extract_iterative(Cells& cells, int NT, int NR, int thr, int rel_num, int rel_den, int R, int maxp,
+                                 uint32_t* cm, hough_peak* dst, int* s_count) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  auto column_best = [&](int j) {
+    uint32_t b = 0;
+    for (int k = lane; k < NR; k += 32) {
+      const uint32_t v = (uint32_t)cells.get(j, k);
+      b = max(b, (v << 16) | (uint32_t)(NR - 1 - k));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    return b;
+  };
+  for (int j = warp; j < NT; j += nwarps) {
+    const uint32_t b = column_best(j);
+    if (lane == 0) cm[j] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t m = 0;
+    for (int j = lane; j < NT; j += 32) m = max(m, cm[j] >> 16);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const long long amax = m;
+    const int W = 2 * R + 1;
+    int n = 0;
+    for (;;) {
+      // across columns only the votes count, then the smaller column (raster order); the
+      // packed row decides within a column
+      uint32_t bv = 0;
+      int bj = NT;
+      for (int j = lane; j < NT; j += 32) {
+        const uint32_t c = cm[j];
+        if ((c >> 16) > (bv >> 16) || bj == NT) {
+          bv = c;
+          bj = j;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if ((ov >> 16) > (bv >> 16) || ((ov >> 16) == (bv >> 16) && oj < bj)) {
+          bv = ov;
+          bj = oj;
+        }
+      }
+      const int v = (int)(bv >> 16);
+      if (v < thr || (long long)v * rel_den < (long long)rel_num * amax) break;
+      const int j = bj, k = NR - 1 - (int)(bv & 0xffffu);
+      if (lane == 0 && n < maxp) {
+        hough_peak pk;
+        pk.theta_bin = (int16_t)j;
+        pk.rho_bin = (int16_t)k;
+        pk.votes = (int16_t)v;
+        pk.flags = 0;
+        dst[n] = pk;
+      }
+      ++n;
+      for (int i = lane; i < W * W; i += 32) {
+        const int dj = i / W - R, dk = i % W - R;
+        int jj = j + dj, kk = k + dk;
+        if (kk < 0 || kk >= NR) continue;
+        if (jj < 0 || jj >= NT) {
+          jj = jj < 0 ? jj + NT : jj - NT;
+          kk = NR - 1 - kk;
+        }
+        cells.clear(jj, kk);
+      }
+      __syncwarp();
+      for (int dj = -R; dj <= R; ++dj) {
+        int jj = j + dj;
+        jj = jj < 0 ? jj + NT : (jj >= NT ? jj - NT : jj);
+        const uint32_t b = column_best(jj);
+        if (lane == 0) cm[jj] = b;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) *s_count = n;
+  }
+  __syncthreads();
+  return *s_count;
+}
+
 __device__ __forceinline__ void flag_status(int* status, int f) {
   if (f) atomicOr(status, f);
 }

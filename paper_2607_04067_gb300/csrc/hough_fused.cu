@@ -381,6 +381,27 @@ __device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, int Wd,
   return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
 }
 
+// Cells of the CTA's accumulator for the iterative finder (one tile): read, and suppress by
+// clearing the cell's half of its word (or the word, with int32 cells).
+template <bool A32>
+struct FusedCells {
+  uint32_t* acc;
+  int Wd, nrp;
+  bool mp;
+  const Plan* pl;
+  __device__ int get(int j, int k) const { return mp ? mp_get(acc, j, k, Wd, *pl) : acc_get<A32>(acc, j, k, nrp); }
+  __device__ void clear(int j, int k) {
+    if (mp) {
+      const bool hi = j >= Wd;
+      atomicAnd(&acc[mp_word(hi ? 2 * Wd - 1 - j : j, k + 1, pl->rows_phys)], hi ? 0x0000ffffu : 0xffff0000u);
+    } else if (A32) {
+      acc[acc_index<true>(j, k, nrp)] = 0u;
+    } else {
+      atomicAnd(&acc[acc_index<false>(j, k, nrp)], (k & 1) ? 0x0000ffffu : 0xffff0000u);
+    }
+  }
+};
+
 // Shared address of the vote whose float row estimate, shifted by 1 + 2^b + e (2^b > N_rho + 1,
 // e = W/2 units of 2^-F, W a power of two), is kfp. In [2^b, 2^(b+1)) a float's low F = 23 - b
 // bits are the fraction and the bits above them (127 + b) 2^b + integer part, so
@@ -1212,94 +1233,119 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   }
   __syncthreads();
 
-  // 3. peak scan
-  unsigned long long csum = 0;
-  const bool packed = !pl.mp && !A32 && (NR & 1) == 0;
-  if (pl.mp) {
-    mp_fold(pl, acc, Wd, T > 1 ? halo : nullptr);
-    __syncthreads();
-    scan_mp(pl, acc, halo, aw, Wd, pbits, do_cs, csum);
-  } else if (packed) {
-    scan_packed(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
-  } else {
-    scan_scalar<A32>(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
-  }
-  __syncthreads();
-
-  // 4. raster-order positions and peak records: keys (column, group of key_words bitmap words)
-  // in raster order, counted from the peak bitmap
-  const int KG = pl.key_groups, G = pl.key_words, nkeys = wt * KG;
-  for (int key = tid; key < nkeys; key += bd) {
-    const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
-    int np = 0;
-    for (int w = w0; w < w1; ++w) np += __popc(pbits[c * pl.nrb + w]);
-    cnt[key] = np;
-  }
-  __syncthreads();
-  const int total = block_exscan(cnt, nkeys, sh.tmp);
-  // peaks of the tile's low columns (mirror-pair tiles: the high columns follow them)
-  const int n_low = (pl.mp && Wd < wt) ? cnt[Wd << pl.key_shift] : total;
-  // event column of tile-local column c: mirror-pair tiles hold [aw, aw + Wd) then
-  // [N - aw - Wd, N - aw), both ascending; other tiles [j0, j0 + wt)
-  const int hi0 = NT - aw - 2 * Wd;
+  // 3-4. peaks
   const int maxp = pl.max_peaks;
-  hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
-  uint2* dst2 = reinterpret_cast<uint2*>(dst);  // records are 8-byte aligned (checked on the host)
-  const int nwarps = bd >> 5;
-  if (G == 1) {
-    // A warp takes 32 consecutive keys (one bitmap word each) and writes their peaks to
-    // consecutive positions: lane i of a pass finds the key owning position P0 + i (the last
-    // lane whose start is <= it) by a shuffle search and the bit by its rank in that word.
-    for (int kb = warp * 32; kb < nkeys; kb += nwarps * 32) {
-      const int key = kb + lane;
-      uint32_t word = 0;
-      int start = total;
-      if (key < nkeys) {
-        const int w = key & (KG - 1);
-        word = (w < pl.nrb) ? pbits[(key >> pl.key_shift) * pl.nrb + w] : 0u;
-        start = cnt[key];
-      }
-      const int P0 = __shfl_sync(kFull, start, 0);
-      const int P1 = min(__shfl_sync(kFull, start + __popc(word), 31), maxp);
-      for (int o0 = P0; o0 < P1; o0 += 32) {
-        const int o = o0 + lane;
-        int l = 0;
-#pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-          const int sc = __shfl_sync(kFull, start, l + st);
-          if (sc <= o) l += st;
-        }
-        const int r = o - __shfl_sync(kFull, start, l);
-        const uint32_t wd = __shfl_sync(kFull, word, l);
-        if (o < P1) {
-          const int kl = kb + l, c = kl >> pl.key_shift;
-          const int k = ((kl & (KG - 1)) << 5) + (int)__fns(wd, 0u, r + 1);
-          const int votes = pl.mp ? mp_get(acc, c, k, Wd, pl) : acc_get<A32>(acc, c, k, nrp);
-          const int col = pl.mp ? (c < Wd ? aw + c : hi0 + c) : j0 + c;
-          dst2[o] = make_uint2((uint32_t)col | ((uint32_t)k << 16), (uint32_t)votes);
-        }
-      }
+  int total = 0, n_low = 0;
+  unsigned long long cs_tile = 0;
+  if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
+    // the paper's iterative finder (one tile, by the plan): the checksum first, then the
+    // extraction, which clears the cells it suppresses; records in extraction order
+    if (pl.mp) {
+      mp_fold(pl, acc, Wd, nullptr);
+      __syncthreads();
     }
+    FusedCells<A32> cells{acc, Wd, nrp, pl.mp != 0, &pl};
+    if (do_cs) {
+      unsigned long long cs = 0;
+      for (int c = tid; c < NT * NR; c += bd) {
+        const int v = cells.get(c / NR, c % NR);
+        if (v) cs += (unsigned long long)v * mix64((unsigned long long)c + 1);
+      }
+      cs_tile = block_sum_u64(cs, sh.red);
+    }
+    __syncthreads();
+    total = extract_iterative(cells, NT, NR, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius, maxp, pbits,
+                              io.peaks + e * (long long)maxp, &sh.total);
+    n_low = total;
   } else {
+    // 3. peak scan
+    unsigned long long csum = 0;
+    const bool packed = !pl.mp && !A32 && (NR & 1) == 0;
+    if (pl.mp) {
+      mp_fold(pl, acc, Wd, T > 1 ? halo : nullptr);
+      __syncthreads();
+      scan_mp(pl, acc, halo, aw, Wd, pbits, do_cs, csum);
+    } else if (packed) {
+      scan_packed(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
+    } else {
+      scan_scalar<A32>(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
+    }
+    __syncthreads();
+
+    // 4. raster-order positions and peak records: keys (column, group of key_words bitmap words)
+    // in raster order, counted from the peak bitmap
+    const int KG = pl.key_groups, G = pl.key_words, nkeys = wt * KG;
     for (int key = tid; key < nkeys; key += bd) {
       const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
-      int pos = cnt[key];
-      for (int w = w0; w < w1 && pos < maxp; ++w) {
-        uint32_t bits = pbits[c * pl.nrb + w];
-        while (bits && pos < maxp) {
-          const int bb = __ffs(bits) - 1;
-          bits &= bits - 1u;
-          const int k = (w << 5) + bb;
-          const int votes = pl.mp ? mp_get(acc, c, k, Wd, pl) : acc_get<A32>(acc, c, k, nrp);
-          const int col = pl.mp ? (c < Wd ? aw + c : hi0 + c) : j0 + c;
-          dst2[pos] = make_uint2((uint32_t)col | ((uint32_t)k << 16), (uint32_t)votes);
-          ++pos;
+      int np = 0;
+      for (int w = w0; w < w1; ++w) np += __popc(pbits[c * pl.nrb + w]);
+      cnt[key] = np;
+    }
+    __syncthreads();
+    total = block_exscan(cnt, nkeys, sh.tmp);
+    // peaks of the tile's low columns (mirror-pair tiles: the high columns follow them)
+    n_low = (pl.mp && Wd < wt) ? cnt[Wd << pl.key_shift] : total;
+    // event column of tile-local column c: mirror-pair tiles hold [aw, aw + Wd) then
+    // [N - aw - Wd, N - aw), both ascending; other tiles [j0, j0 + wt)
+    const int hi0 = NT - aw - 2 * Wd;
+    hough_peak* dst = (T == 1) ? io.peaks + e * (long long)maxp : io.tile_peaks + (e * T + t) * (long long)maxp;
+    uint2* dst2 = reinterpret_cast<uint2*>(dst);  // records are 8-byte aligned (checked on the host)
+    const int nwarps = bd >> 5;
+    if (G == 1) {
+      // A warp takes 32 consecutive keys (one bitmap word each) and writes their peaks to
+      // consecutive positions: lane i of a pass finds the key owning position P0 + i (the last
+      // lane whose start is <= it) by a shuffle search and the bit by its rank in that word.
+      for (int kb = warp * 32; kb < nkeys; kb += nwarps * 32) {
+        const int key = kb + lane;
+        uint32_t word = 0;
+        int start = total;
+        if (key < nkeys) {
+          const int w = key & (KG - 1);
+          word = (w < pl.nrb) ? pbits[(key >> pl.key_shift) * pl.nrb + w] : 0u;
+          start = cnt[key];
+        }
+        const int P0 = __shfl_sync(kFull, start, 0);
+        const int P1 = min(__shfl_sync(kFull, start + __popc(word), 31), maxp);
+        for (int o0 = P0; o0 < P1; o0 += 32) {
+          const int o = o0 + lane;
+          int l = 0;
+  #pragma unroll
+          for (int st = 16; st > 0; st >>= 1) {
+            const int sc = __shfl_sync(kFull, start, l + st);
+            if (sc <= o) l += st;
+          }
+          const int r = o - __shfl_sync(kFull, start, l);
+          const uint32_t wd = __shfl_sync(kFull, word, l);
+          if (o < P1) {
+            const int kl = kb + l, c = kl >> pl.key_shift;
+            const int k = ((kl & (KG - 1)) << 5) + (int)__fns(wd, 0u, r + 1);
+            const int votes = pl.mp ? mp_get(acc, c, k, Wd, pl) : acc_get<A32>(acc, c, k, nrp);
+            const int col = pl.mp ? (c < Wd ? aw + c : hi0 + c) : j0 + c;
+            dst2[o] = make_uint2((uint32_t)col | ((uint32_t)k << 16), (uint32_t)votes);
+          }
+        }
+      }
+    } else {
+      for (int key = tid; key < nkeys; key += bd) {
+        const int c = key >> pl.key_shift, w0 = (key & (KG - 1)) * G, w1 = min(pl.nrb, w0 + G);
+        int pos = cnt[key];
+        for (int w = w0; w < w1 && pos < maxp; ++w) {
+          uint32_t bits = pbits[c * pl.nrb + w];
+          while (bits && pos < maxp) {
+            const int bb = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const int k = (w << 5) + bb;
+            const int votes = pl.mp ? mp_get(acc, c, k, Wd, pl) : acc_get<A32>(acc, c, k, nrp);
+            const int col = pl.mp ? (c < Wd ? aw + c : hi0 + c) : j0 + c;
+            dst2[pos] = make_uint2((uint32_t)col | ((uint32_t)k << 16), (uint32_t)votes);
+            ++pos;
+          }
         }
       }
     }
+    cs_tile = do_cs ? block_sum_u64(csum, sh.red) : 0ull;
+    __syncthreads();
   }
-  const unsigned long long cs_tile = do_cs ? block_sum_u64(csum, sh.red) : 0ull;
-  __syncthreads();
 
   // 5. tiles: publish, and let the last tile of the event merge
   int ev_total = total;
@@ -1368,7 +1414,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     for (long long i = tid; i < nll; i += bd) io.mask[a + i] = 0;
   } else {
     kept = select_event(pl, io, smem, sh, tc, ts, a, n, io.peaks + e * (long long)maxp, min(ev_total, maxp),
-                        T == 1 && ev_total <= maxp && pl.keep_hw < 32);
+                        pl.peak_mode == HOUGH_PEAK_LOCAL_MAX && T == 1 && ev_total <= maxp && pl.keep_hw < 32);
   }
   if (tid == 0) sh.kept_tot = 0;
   __syncthreads();

@@ -13,6 +13,7 @@ namespace hgpu {
 // Launch shape and shared-memory layout of the fused kernel for one parameter set.
 struct Plan {
   int n_theta, n_rho, threshold, keep_hw, max_peaks;
+  int peak_mode, rel_num, rel_den, nms_radius;  // peak finder (0: 3x3 local maxima, 1: iterative)
   int tiles;      // theta tiles per event
   int tile_w;     // columns per tile (last tile may be narrower)
   int groups;     // 32-column groups per tile

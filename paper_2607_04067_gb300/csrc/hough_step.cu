@@ -293,6 +293,40 @@ __global__ void circles_kernel(const int* __restrict__ npeaks, const hough_peak*
   }
 }
 
+// The iterative finder on an accumulator in HBM (read only): suppressed cells are kept in a
+// shared-memory bitmap, one CTA per event.
+struct GlobalCells {
+  const int16_t* A;
+  uint32_t* gone;
+  int NR;
+  __device__ int get(int j, int k) const {
+    const int c = j * NR + k;
+    return ((gone[c >> 5] >> (c & 31)) & 1u) ? 0 : (int)A[c];
+  }
+  __device__ void clear(int j, int k) {
+    const int c = j * NR + k;
+    atomicOr(&gone[c >> 5], 1u << (c & 31));
+  }
+};
+
+__global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, int NR, int thr, int rel_num,
+                                       int rel_den, int R, int maxp, int* npeaks, hough_peak* peaks, int* status) {
+  extern __shared__ uint32_t sm[];
+  __shared__ int s_count;
+  const long long e = blockIdx.x;
+  uint32_t* cm = sm;
+  uint32_t* gone = sm + NT;
+  const int nwords = (NT * NR + 31) >> 5;
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) gone[i] = 0u;
+  __syncthreads();
+  GlobalCells cells{acc + e * (long long)NT * NR, gone, NR};
+  const int n = extract_iterative(cells, NT, NR, thr, rel_num, rel_den, R, maxp, cm, peaks + e * maxp, &s_count);
+  if (threadIdx.x == 0) {
+    npeaks[e] = n;
+    if (n > maxp) atomicOr(status, HOUGH_F_PEAK_OVERFLOW);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_map(const int2* xy, long long n_hits, long long* uq, long long* vq, int* status, cudaStream_t st) {
@@ -322,6 +356,16 @@ cudaError_t launch_vote(const long long* uq, const long long* vq, const long lon
 cudaError_t launch_peaks(const int16_t* acc, long long n_events, const hough_params& p, int* npeaks,
                          hough_peak* peaks, int* status, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;
+  if (p.peak_mode == HOUGH_PEAK_ITERATIVE) {
+    const int smem = (p.n_theta + (p.n_theta * p.n_rho + 31) / 32) * 4;
+    cudaError_t err = cudaFuncSetAttribute((const void*)peaks_iterative_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    peaks_iterative_kernel<<<(unsigned)n_events, 512, smem, st>>>(acc, p.n_theta, p.n_rho, p.threshold, p.rel_num,
+                                                                  p.rel_den, p.nms_radius, p.max_peaks, npeaks,
+                                                                  peaks, status);
+    return cudaGetLastError();
+  }
   peaks_kernel<<<(unsigned)n_events, 256, 0, st>>>(acc, p.n_theta, p.n_rho, p.threshold, p.max_peaks, npeaks, peaks,
                                                    status);
   return cudaGetLastError();

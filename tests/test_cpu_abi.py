@@ -43,10 +43,20 @@ def test_resolve_and_reject_params():
     r = h.resolve(h.params(256, 256, 16, theta_tiles=4, block=0))
     assert r.theta_tiles == 4 and r.block == 2 * 32 * (r.block // 64) + 32 or r.block <= 1024
     for bad in (h.params(3, 64, 1), h.params(64, 2000, 1), h.params(64, 64, 0), h.params(64, 64, 1, -1),
-                h.params(64, 64, 1, max_peaks=0), h.params(64, 64, 1, theta_tiles=100), h.params(64, 64, 1, block=33)):
+                h.params(64, 64, 1, max_peaks=0), h.params(64, 64, 1, theta_tiles=100), h.params(64, 64, 1, block=33),
+                h.params(64, 64, 1, peak_mode=2), h.params(64, 64, 1, peak_mode=1, rel_den=0),
+                h.params(64, 64, 1, peak_mode=1, rel_num=3, rel_den=2),
+                h.params(64, 64, 1, peak_mode=1, nms_radius=32), h.params(64, 64, 1, peak_mode=1, nms_radius=-1),
+                h.params(256, 256, 16, peak_mode=1, theta_tiles=2)):
         with pytest.raises(h.HoughError) as ei:
             h.resolve(bad)
         assert ei.value.code == h.EPARAM
+    # the iterative finder keeps the accumulator in one CTA
+    r = h.resolve(h.params(256, 256, 16, max_peaks=4096, peak_mode=1, rel_num=1, rel_den=2, nms_radius=3))
+    assert r.theta_tiles == 1 and r.peak_mode == 1 and r.rel_den == 2 and r.nms_radius == 3
+    with pytest.raises(h.HoughError) as ei:
+        h.resolve(h.params(512, 512, 20, peak_mode=1, rel_num=1, rel_den=2))
+    assert ei.value.code == h.ESMEM
 
 
 def test_workspace_sizes(lib):

@@ -400,3 +400,54 @@ def test_circles_odd_rho_and_field(h):
     fin = np.isfinite(ref)
     np.testing.assert_allclose(got[fin], ref[fin], rtol=1e-6)
     assert np.array_equal(np.sign(got[~fin]), np.sign(ref[~fin]))
+
+
+# ---------------------------------------------------------------- iterative peak finder (Sec. 2)
+
+ITER = [  # (workload, events, n_theta, n_rho, threshold, rel_num, rel_den, nms_radius, max_peaks)
+    ("plain_paper", 60, 256, 256, 16, 1, 2, 3, 64),
+    ("plain_paper", 40, 64, 64, 8, 1, 3, 1, 256),
+    ("batched", 60, 256, 256, 16, 2, 5, 2, 128),
+    ("plain_small", 30, 64, 64, 6, 0, 1, 0, 300),    # no relative cut, no neighbourhood: every cell >= T
+    ("plain_paper", 30, 100, 63, 8, 1, 4, 2, 512),   # N_theta not a multiple of 64, odd N_rho
+    ("plain_paper", 20, 256, 256, 16, 1, 10, 1, 8),  # overflow: more peaks than stored
+]
+
+
+@pytest.mark.parametrize("name,n,nt,nr,thr,num,den,R,mx", ITER)
+def test_iterative_fused_and_stepwise_match_oracle(h, name, n, nt, nr, thr, num, den, R, mx):
+    cfg = gen.CONFIGS[name]
+    ev = gen.generate(cfg, n)
+    op = oracle.params(nt, nr, thr, 1, mx, peak_mode=1, rel_num=num, rel_den=den, nms_radius=R)
+    ref = oracle.run(ev.xy, ev.off, op, with_acc=True, threads=THREADS)
+    xy, off = dev(ev)
+    p = h.params(nt, nr, thr, 1, mx, peak_mode=1, rel_num=num, rel_den=den, nms_radius=R)
+    for batched in (False, True):
+        out = h.run(xy, off, p, checksum=True, batched=batched)
+        assert h.status(out.status) == ref.status
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, checksum=out.checksum)
+    # stepwise: the iterative finder on the oracle's accumulator in HBM
+    st = h.new_status()
+    acc = torch.from_numpy(ref.acc).cuda()
+    npk, pk = h.peaks(acc, p, st)
+    assert np.array_equal(to_np(npk), ref.npeaks)
+    assert np.array_equal(peaks_np(pk), peaks_np(torch.from_numpy(ref.peaks.view(np.int16).reshape(n, mx, 4))))
+
+
+def test_iterative_stepwise_large_accumulator(h):
+    """1000 x 1000 (2 MB accumulator, no single-CTA fused plan): the stepwise finder keeps its
+    suppression bitmap in shared memory."""
+    cfg = gen.CONFIGS["paper_1000"]
+    ev = gen.generate(cfg, 6)
+    op = oracle.params(1000, 1000, 12, 1, 256, peak_mode=1, rel_num=1, rel_den=2, nms_radius=4)
+    ref = oracle.run(ev.xy, ev.off, op, with_acc=True, threads=THREADS)
+    p = h.params(1000, 1000, 12, 1, 256, peak_mode=1, rel_num=1, rel_den=2, nms_radius=4)
+    st = h.new_status()
+    npk, pk = h.peaks(torch.from_numpy(ref.acc).cuda(), p, st)
+    assert h.status(st) == 0
+    assert np.array_equal(to_np(npk), ref.npeaks)
+    n = ref.npeaks
+    got = peaks_np(pk)
+    exp = peaks_np(torch.from_numpy(ref.peaks.view(np.int16).reshape(len(n), 256, 4)))
+    for e in range(len(n)):
+        assert np.array_equal(got[e][: min(n[e], 256)], exp[e][: min(n[e], 256)])
