@@ -129,13 +129,21 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
-def oracle_baseline(cfg, ev, budget_events: int, threads: int):
+def peak_args(args):
+    """(peak_mode, rel_num, rel_den, nms_radius) of the command line."""
+    if getattr(args, "peak_mode", "local-max") != "iterative":
+        return 0, 0, 1, 1
+    num, den = (int(x) for x in args.rel.split("/"))
+    return 1, num, den, args.nms_radius
+
+
+def oracle_baseline(cfg, ev, budget_events: int, threads: int, peak=(0, 0, 1, 1)):
     """The CPU oracle as it stands, timed on the host cores over the first events of the batch."""
     import oracle
     n = min(budget_events, ev.n_events)
     off = ev.off[: n + 1]
     xy = ev.xy[: int(off[-1])]
-    p = oracle.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks)
+    p = oracle.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks, *peak)
     t0 = time.perf_counter()
     r = oracle.run(xy, off, p, threads=threads)
     dt = time.perf_counter() - t0
@@ -150,10 +158,10 @@ def run_reference(args, cfg):
     per_step = args.ref_events
     ev = gen.generate(cfg, per_step, with_truth=False)
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle_baseline(cfg, ev, per_step, threads)
+        oracle_baseline(cfg, ev, per_step, threads, peak_args(args))
     times = []
     for _ in range(args.steps):
-        _, _, n, dt = oracle_baseline(cfg, ev, per_step, threads)
+        _, _, n, dt = oracle_baseline(cfg, ev, per_step, threads, peak_args(args))
         times.append(dt)
     total = sum(times)
     value = per_step * args.steps / total
@@ -347,6 +355,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
     ap.add_argument("--shape", default="", help="fixed launch shape 'theta_tiles,block,events_per_cta' (profiling)")
+    ap.add_argument("--peak-mode", default="local-max", choices=["local-max", "iterative"],
+                    help="peak finder: one-pass 3x3 local maxima, or the paper's iterative finder")
+    ap.add_argument("--rel", default="1/2", help="iterative finder: relative threshold as a fraction of the maximum")
+    ap.add_argument("--nms-radius", type=int, default=3, help="iterative finder: suppression half-width in bins")
     ap.add_argument("--physics-events", type=int, default=2000,
                     help="events whose peaks are matched to the true tracks (Eq. 2 circles)")
     ap.add_argument("--sweep", default="", help="batch-size sweep instead of the benchmark, e.g. '1,10,100,1000'")
@@ -379,6 +391,7 @@ def main():
     xy = torch.from_numpy(ev.xy).cuda()
     off = torch.from_numpy(ev.off).cuda()
     p = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks)
+    p.peak_mode, p.rel_num, p.rel_den, p.nms_radius = peak_args(args)
     tune_ms = None
     if args.shape:
         p.theta_tiles, p.block, p.events_per_cta = (int(x) for x in args.shape.split(","))
@@ -475,8 +488,8 @@ def main():
     cpu = None
     if not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, _, n, dt = oracle_baseline(cfg, ev, args.cpu_sample, threads)
-        v1, _, n1, dt1 = oracle_baseline(cfg, ev, max(1, args.cpu_sample // 10), 1)
+        v, _, n, dt = oracle_baseline(cfg, ev, args.cpu_sample, threads, peak_args(args))
+        v1, _, n1, dt1 = oracle_baseline(cfg, ev, max(1, args.cpu_sample // 10), 1, peak_args(args))
         cpu = {"value": v, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"first {n} events of this batch ({dt:.1f} s wall on {threads} threads, events in parallel)",
                "single_thread": {"value": v1, "unit": "events/s", "cores": 1,
@@ -496,6 +509,9 @@ def main():
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": cfg.name, "events_per_gpu": n_events, "hits_per_gpu": ev.n_hits,
                    "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
+                   "peak_finder": ("3x3 local maxima" if args.peak_mode == "local-max" else
+                                   f"iterative, relative threshold {args.rel} of the maximum, "
+                                   f"suppression radius {args.nms_radius}"),
                    "max_peaks": cfg.max_peaks, "launch": {"theta_tiles": plan.theta_tiles, "block": plan.block,
                                                           "events_per_cta": plan.events_per_cta,
                                                           "autotuned": not (args.no_tune or args.shape),
