@@ -102,15 +102,15 @@ __device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
 // Iterative peak extraction (the paper's finder, Sec. 2) over an accumulator behind `cells`
 // (get(j, k) -> votes of a cell not yet suppressed, 0 once suppressed; clear(j, k) suppresses).
 // cm: n_theta words of shared scratch holding each column's best cell packed as
-// (votes << 16) | (n_rho - 1 - k), so that the larger word is the cell with more votes and, on
-// equal votes, the smaller k. The whole CTA fills cm; warp 0 then extracts: the column word
-// with the most votes (equal votes: the smaller column) is the next peak if it qualifies, its window is
-// cleared and the 2R + 1 columns it touches are re-scanned. Every pass clears the extracted
-// cell, so the loop ends. Records go to dst in extraction order (the first max_peaks);
-// returns the true count (valid in every thread).
+// (votes << 16) | (n_rho - 1 - k): within a column the larger word is the cell with more votes
+// and, on equal votes, the smaller k. s: 2 ints of shared scratch. Each pass: warp 0 takes the
+// column with the most votes (equal votes: the smaller column, i.e. raster order); if that cell
+// qualifies it is the next peak, the whole CTA clears its window and warps re-scan the 2R + 1
+// columns it touches, one column per warp. Every pass clears the extracted cell, so the loop
+// ends. Records go to dst in extraction order (the first max_peaks); returns the true count.
 template <class Cells>
 __device__ int extract_iterative(Cells& cells, int NT, int NR, int thr, int rel_num, int rel_den, int R, int maxp,
-                                 uint32_t* cm, hough_peak* dst, int* s_count) {
+                                 uint32_t* cm, hough_peak* dst, int* s) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   auto column_best = [&](int j) {
     uint32_t b = 0;
@@ -127,17 +127,18 @@ __device__ int extract_iterative(Cells& cells, int NT, int NR, int thr, int rel_
     if (lane == 0) cm[j] = b;
   }
   __syncthreads();
-  if (warp == 0) {
+  long long amax = 0;
+  {
     uint32_t m = 0;
     for (int j = lane; j < NT; j += 32) m = max(m, cm[j] >> 16);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const long long amax = m;
-    const int W = 2 * R + 1;
-    int n = 0;
-    for (;;) {
-      // across columns only the votes count, then the smaller column (raster order); the
-      // packed row decides within a column
+    amax = m;  // every warp computes the same maximum
+  }
+  const int W = 2 * R + 1;
+  int n = 0;
+  for (;;) {
+    if (warp == 0) {
       uint32_t bv = 0;
       int bj = NT;
       for (int j = lane; j < NT; j += 32) {
@@ -157,40 +158,44 @@ __device__ int extract_iterative(Cells& cells, int NT, int NR, int thr, int rel_
         }
       }
       const int v = (int)(bv >> 16);
-      if (v < thr || (long long)v * rel_den < (long long)rel_num * amax) break;
-      const int j = bj, k = NR - 1 - (int)(bv & 0xffffu);
-      if (lane == 0 && n < maxp) {
-        hough_peak pk;
-        pk.theta_bin = (int16_t)j;
-        pk.rho_bin = (int16_t)k;
-        pk.votes = (int16_t)v;
-        pk.flags = 0;
-        dst[n] = pk;
-      }
-      ++n;
-      for (int i = lane; i < W * W; i += 32) {
-        const int dj = i / W - R, dk = i % W - R;
-        int jj = j + dj, kk = k + dk;
-        if (kk < 0 || kk >= NR) continue;
-        if (jj < 0 || jj >= NT) {
-          jj = jj < 0 ? jj + NT : jj - NT;
-          kk = NR - 1 - kk;
+      const bool ok = bj < NT && v >= thr && (long long)v * rel_den >= (long long)rel_num * amax;
+      if (lane == 0) {
+        s[0] = ok ? bj : -1;
+        s[1] = ok ? NR - 1 - (int)(bv & 0xffffu) : 0;
+        if (ok && n < maxp) {
+          hough_peak pk;
+          pk.theta_bin = (int16_t)bj;
+          pk.rho_bin = (int16_t)(NR - 1 - (int)(bv & 0xffffu));
+          pk.votes = (int16_t)v;
+          pk.flags = 0;
+          dst[n] = pk;
         }
-        cells.clear(jj, kk);
       }
-      __syncwarp();
-      for (int dj = -R; dj <= R; ++dj) {
-        int jj = j + dj;
-        jj = jj < 0 ? jj + NT : (jj >= NT ? jj - NT : jj);
-        const uint32_t b = column_best(jj);
-        if (lane == 0) cm[jj] = b;
-      }
-      __syncwarp();
     }
-    if (lane == 0) *s_count = n;
+    __syncthreads();
+    const int j = s[0], k = s[1];
+    if (j < 0) break;
+    ++n;
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
+      const int dj = i / W - R, dk = i % W - R;
+      int jj = j + dj, kk = k + dk;
+      if (kk < 0 || kk >= NR) continue;
+      if (jj < 0 || jj >= NT) {
+        jj = jj < 0 ? jj + NT : jj - NT;
+        kk = NR - 1 - kk;
+      }
+      cells.clear(jj, kk);
+    }
+    __syncthreads();
+    for (int dj = warp - R; dj <= R; dj += nwarps) {
+      int jj = j + dj;
+      jj = jj < 0 ? jj + NT : (jj >= NT ? jj - NT : jj);
+      const uint32_t b = column_best(jj);
+      if (lane == 0) cm[jj] = b;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  return *s_count;
+  return n;
 }
 
 __device__ __forceinline__ void flag_status(int* status, int f) {

@@ -1255,7 +1255,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     }
     __syncthreads();
     total = extract_iterative(cells, NT, NR, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius, maxp, pbits,
-                              io.peaks + e * (long long)maxp, &sh.total);
+                              io.peaks + e * (long long)maxp, sh.tmp);
     n_low = total;
   } else {
     // 3. peak scan

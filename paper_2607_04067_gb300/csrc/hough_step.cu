@@ -312,7 +312,7 @@ struct GlobalCells {
 __global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, int NR, int thr, int rel_num,
                                        int rel_den, int R, int maxp, int* npeaks, hough_peak* peaks, int* status) {
   extern __shared__ uint32_t sm[];
-  __shared__ int s_count;
+  __shared__ int s_sel[2];
   const long long e = blockIdx.x;
   uint32_t* cm = sm;
   uint32_t* gone = sm + NT;
@@ -320,7 +320,7 @@ __global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, 
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) gone[i] = 0u;
   __syncthreads();
   GlobalCells cells{acc + e * (long long)NT * NR, gone, NR};
-  const int n = extract_iterative(cells, NT, NR, thr, rel_num, rel_den, R, maxp, cm, peaks + e * maxp, &s_count);
+  const int n = extract_iterative(cells, NT, NR, thr, rel_num, rel_den, R, maxp, cm, peaks + e * maxp, s_sel);
   if (threadIdx.x == 0) {
     npeaks[e] = n;
     if (n > maxp) atomicOr(status, HOUGH_F_PEAK_OVERFLOW);
