@@ -680,6 +680,8 @@ void hough_set_stage_events(void* begin, void* end) {
 }
 
 namespace {
+constexpr int kHostChunks = 8;  // most event chunks of one hough_run_host call
+
 struct HostLayout {
   size_t xy, off, npeaks, peaks, mask, nkept, peak_off, dense, ws, ws_bytes, total;
 };
@@ -695,12 +697,12 @@ bool host_layout(const hough_params* p, int64_t n_hits, int64_t n_events, HostLa
     return at;
   };
   L.xy = take(8 * nh);
-  L.off = take(8 * (ne + 1));
+  L.off = take(8 * (ne + 1 + kHostChunks));  // per chunk its own rebased offsets
   L.npeaks = take(4 * ne);
   L.peaks = take(sizeof(hough_peak) * ne * mp);
   L.mask = take(nh);
   L.nkept = take(4 * ne);
-  L.peak_off = take(8 * (ne + 1));
+  L.peak_off = take(8 * (ne + 1 + kHostChunks));
   L.dense = take(sizeof(hough_peak) * ne * mp);
   L.ws_bytes = ws_layout(pl, n_events).total;
   L.ws = take(L.ws_bytes);
@@ -714,6 +716,34 @@ size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_e
   return host_layout(p, n_hits, n_events, L) ? L.total : 256;
 }
 
+// Streams and events of the pipelined host path, per host thread and device.
+struct HostPipe {
+  int device = -1;
+  cudaStream_t in = nullptr, out = nullptr, peaks = nullptr;
+  cudaEvent_t ev[3 * kHostChunks] = {};
+  bool ok = false;
+};
+
+static HostPipe& host_pipe() {
+  thread_local HostPipe hp;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!hp.ok || hp.device != dev) {
+    hp.ok = cudaStreamCreateWithFlags(&hp.in, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&hp.out, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&hp.peaks, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 3 * kHostChunks && hp.ok; ++i)
+      hp.ok = cudaEventCreateWithFlags(&hp.ev[i], cudaEventDisableTiming) == cudaSuccess;
+    hp.device = dev;
+  }
+  return hp;
+}
+
+// The batch is cut into up to kHostChunks event ranges that flow through four streams:
+// copy-in (hits and offsets, rebased to the chunk), compute on `stream` (the batched path
+// and the peak packing), copy-out (counts, mask, offsets) and, once a chunk's counts are on
+// the host, a peak stream that copies exactly its stored peaks, so every transfer overlaps
+// the kernels of other chunks.
 int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, int64_t n_events, const hough_params* p,
                    int32_t* h_npeaks, int64_t* h_peak_off, hough_peak* h_peaks, int64_t h_peaks_cap, uint8_t* h_mask,
                    int32_t* h_nkept, void* d_buf, size_t d_buf_bytes, int32_t* d_status, void* stream) {
@@ -728,34 +758,82 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
   HostLayout L;
   if (!host_layout(p, n_hits, n_events, L)) return HOUGH_EPARAM;
   if (d_buf_bytes < L.total) return HOUGH_EWORKSPACE;
+  if (h_off[0] != 0 || h_off[n_events] != n_hits) return HOUGH_EINVAL;
+  for (int64_t e = 0; e < n_events; ++e)
+    if (h_off[e + 1] < h_off[e]) return HOUGH_EINVAL;
+  HostPipe& hp = host_pipe();
+  if (!hp.ok) return cuda_fail(cudaGetLastError());
   char* b = (char*)d_buf;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t ne = (size_t)n_events, nh = (size_t)n_hits;
-  cudaError_t e = cudaMemcpyAsync(b + L.xy, h_xy, 8 * nh, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b + L.off, h_off, 8 * (ne + 1), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e);
-  rc = hough_run_batched((const int32_t*)(b + L.xy), n_hits, (const int64_t*)(b + L.off), n_events, p,
-                         (int32_t*)(b + L.npeaks), (hough_peak*)(b + L.peaks), (uint8_t*)(b + L.mask),
-                         (int32_t*)(b + L.nkept), nullptr, b + L.ws, L.ws_bytes, d_status, stream);
-  if (rc) return rc;
-  e = launch_pack_peaks((const int*)(b + L.npeaks), (const hough_peak*)(b + L.peaks), n_events, p->max_peaks,
-                        (long long*)(b + L.peak_off), (hough_peak*)(b + L.dense), st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_npeaks, b + L.npeaks, 4 * ne, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_nkept, b + L.nkept, 4 * ne, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && nh) e = cudaMemcpyAsync(h_mask, b + L.mask, nh, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_peak_off, b + L.peak_off, 8 * (ne + 1), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e);
-  const int64_t total = h_peak_off[ne];
-  if (total > h_peaks_cap) return HOUGH_EWORKSPACE;
-  if (total > 0) {
-    e = cudaMemcpyAsync(h_peaks, b + L.dense, sizeof(hough_peak) * (size_t)total, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(e);
+  const size_t mp = (size_t)p->max_peaks;
+  // chunk c: events [ce[c], ce[c + 1])
+  const int K = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n_events / 2048));
+  int64_t ce[kHostChunks + 1];
+  for (int c = 0; c <= K; ++c) ce[c] = n_events * c / K;
+  cudaError_t e = cudaSuccess;
+  int32_t* d_npk = (int32_t*)(b + L.npeaks);
+  int32_t* d_nk = (int32_t*)(b + L.nkept);
+  int64_t* d_off = (int64_t*)(b + L.off);
+  int64_t* d_poff = (int64_t*)(b + L.peak_off);
+  hough_peak* d_pk = (hough_peak*)(b + L.peaks);
+  hough_peak* d_dense = (hough_peak*)(b + L.dense);
+  uint8_t* d_mask = (uint8_t*)(b + L.mask);
+  const int32_t* d_xy = (const int32_t*)(b + L.xy);
+  // the compute stream's earlier work must not see half-written inputs: copy-in starts after it
+  e = cudaEventRecord(hp.ev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.ev[0], 0);
+  for (int c = 0; c < K && e == cudaSuccess; ++c) {
+    const int64_t e0 = ce[c], n = ce[c + 1] - ce[c], a0 = h_off[e0], nh = h_off[ce[c + 1]] - a0;
+    int64_t* roff = d_off + e0 + c;
+    cudaEvent_t ev_in = hp.ev[3 * c], ev_comp = hp.ev[3 * c + 1], ev_out = hp.ev[3 * c + 2];
+    e = cudaMemcpyAsync(roff, h_off + e0, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, hp.in);
+    if (e == cudaSuccess && nh)
+      e = cudaMemcpyAsync((char*)d_xy + 8 * (size_t)a0, h_xy + 2 * a0, 8 * (size_t)nh, cudaMemcpyHostToDevice, hp.in);
+    if (e == cudaSuccess) e = launch_rebase((long long*)roff, n + 1, a0, hp.in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, hp.in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in, 0);
+    if (e != cudaSuccess) break;
+    rc = hough_run_batched(d_xy + 2 * a0, nh, roff, n, p, d_npk + e0, d_pk + e0 * mp, d_mask + a0, d_nk + e0,
+                           nullptr, b + L.ws, L.ws_bytes, d_status, stream);
+    if (rc) return rc;
+    e = launch_pack_peaks(d_npk + e0, d_pk + e0 * mp, n, p->max_peaks, (long long*)(d_poff + e0 + c),
+                          d_dense + e0 * mp, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_comp, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.out, ev_comp, 0);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(h_npeaks + e0, d_npk + e0, 4 * (size_t)n, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(h_nkept + e0, d_nk + e0, 4 * (size_t)n, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess && nh) e = cudaMemcpyAsync(h_mask + a0, d_mask + a0, (size_t)nh, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess && n)
+      e = cudaMemcpyAsync(h_peak_off + e0, d_poff + e0 + c, 8 * (size_t)n, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out, hp.out);
   }
+  // stored peaks, chunk by chunk, as each chunk's counts arrive
+  int64_t base = 0;
+  bool over = false;
+  for (int c = 0; c < K && e == cudaSuccess; ++c) {
+    const int64_t e0 = ce[c], n = ce[c + 1] - ce[c];
+    e = cudaEventSynchronize(hp.ev[3 * c + 2]);
+    if (e != cudaSuccess) break;
+    int64_t tot = 0;
+    for (int64_t i = e0; i < e0 + n; ++i) {
+      h_peak_off[i] += base;
+      tot += std::min<int64_t>(h_npeaks[i], (int64_t)mp);
+    }
+    if (base + tot > h_peaks_cap) over = true;
+    // the chunk's packing finished before its counts were copied, which the host has seen
+    if (!over && tot > 0)
+      e = cudaMemcpyAsync(h_peaks + base, d_dense + e0 * mp, sizeof(hough_peak) * (size_t)tot,
+                          cudaMemcpyDeviceToHost, hp.peaks);
+    base += tot;
+  }
+  h_peak_off[n_events] = base;
   int32_t flags = 0;
-  e = cudaMemcpyAsync(&flags, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, hp.out);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(hp.out);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(hp.peaks);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
+  if (over) return HOUGH_EWORKSPACE;
   return flags ? HOUGH_EDEVICE : HOUGH_OK;
 }
 

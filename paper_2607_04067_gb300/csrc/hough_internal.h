@@ -90,6 +90,7 @@ cudaError_t launch_select(const long long* uq, const long long* vq, const long l
 
 cudaError_t launch_circles(const int* npeaks, const hough_peak* peaks, long long n_events, int n_theta, int n_rho,
                            int max_peaks, double b_tesla, float* circles, cudaStream_t st);
+cudaError_t launch_rebase(long long* off, long long n, long long a0, cudaStream_t st);
 cudaError_t launch_pack_peaks(const int* npeaks, const hough_peak* peaks, long long n_events, int max_peaks,
                               long long* peak_off, hough_peak* dense, cudaStream_t st);
 

@@ -1,6 +1,7 @@
 // Stepwise kernels: the same path as the fused kernel, with every intermediate in HBM
 // (u_q/v_q, the full int16 accumulator, the peak lists). They exist so that each step
 // can be checked on its own against the CPU oracle; they favour plain code over speed.
+#include <algorithm>
 #include <climits>
 
 #include "hough_internal.h"
@@ -327,6 +328,12 @@ __global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, 
   }
 }
 
+// Offsets of a chunk of a batch, made relative to the chunk's first hit.
+__global__ void rebase_kernel(long long* off, long long n, long long a0) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    off[i] -= a0;
+}
+
 }  // namespace
 
 cudaError_t launch_map(const int2* xy, long long n_hits, long long* uq, long long* vq, int* status, cudaStream_t st) {
@@ -387,6 +394,13 @@ cudaError_t launch_circles(const int* npeaks, const hough_peak* peaks, long long
   const long long blocks = min((total + 255) / 256, 152LL * 16);
   circles_kernel<<<(unsigned)blocks, 256, 0, st>>>(npeaks, peaks, n_events, n_theta, n_rho, max_peaks, b_tesla,
                                                    reinterpret_cast<float4*>(circles));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rebase(long long* off, long long n, long long a0, cudaStream_t st) {
+  if (n <= 0 || a0 == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 8);
+  rebase_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n, a0);
   return cudaGetLastError();
 }
 

@@ -451,3 +451,50 @@ def test_iterative_stepwise_large_accumulator(h):
     exp = peaks_np(torch.from_numpy(ref.peaks.view(np.int16).reshape(len(n), 256, 4)))
     for e in range(len(n)):
         assert np.array_equal(got[e][: min(n[e], 256)], exp[e][: min(n[e], 256)])
+
+
+# ---------------------------------------------------------------- host-buffer path (pipelined chunks)
+
+@pytest.mark.parametrize("name,n", [("plain_paper", 300), ("batched", 9000), ("stress", 4100)])
+def test_host_path_matches_oracle(h, name, n):
+    """hough_run_host: pinned host inputs in, host results out. 9,000 and 4,100 events run as
+    several pipelined chunks (rebased offsets, peaks packed per chunk and re-based on the host)."""
+    cfg = gen.CONFIGS[name]
+    ev = gen.generate(cfg, n)
+    ref = oracle_of(cfg, ev)
+    p = cfg_params(h, cfg)
+    r = h.HostRunner(ev.n_hits, ev.n_events, p)
+    xy = torch.from_numpy(ev.xy).pin_memory()
+    off = torch.from_numpy(ev.off).pin_memory()
+    for _ in range(2):  # a second call reuses the cached graphs and streams
+        assert r(xy, off) == 0
+        assert np.array_equal(r.npeaks.numpy(), ref.npeaks)
+        assert np.array_equal(r.nkept.numpy(), ref.nkept)
+        assert np.array_equal(r.mask.numpy()[: ev.n_hits], ref.mask)
+        po = r.peak_off.numpy()
+        stored = np.minimum(ref.npeaks, cfg.max_peaks)
+        assert po[0] == 0 and np.array_equal(np.diff(po), stored)
+        dense = r.peaks.numpy()[: po[-1]].astype(np.int16).view(oracle.PEAK_DTYPE).reshape(-1)
+        for e in range(n):
+            assert np.array_equal(dense[po[e]: po[e + 1]], ref.peaks[e, : stored[e]]), e
+
+
+def test_host_path_errors(h):
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 50)
+    p = cfg_params(h, cfg)
+    xy = torch.from_numpy(ev.xy).pin_memory()
+    off = torch.from_numpy(ev.off).pin_memory()
+    small = h.HostRunner(ev.n_hits, ev.n_events, p, peaks_cap=10)
+    with pytest.raises(h.HoughError) as ei:
+        small(xy, off)
+    assert ei.value.code == h.EWORKSPACE
+    ref = oracle_of(cfg, ev)
+    assert np.array_equal(small.npeaks.numpy(), ref.npeaks)  # counts and offsets still valid
+    assert small.peak_off.numpy()[-1] == np.minimum(ref.npeaks, cfg.max_peaks).sum()
+    bad = off.clone()
+    bad[10] = bad[11] + 1  # offsets must not decrease: refused on the host, nothing enqueued
+    r = h.HostRunner(ev.n_hits, ev.n_events, p)
+    with pytest.raises(h.HoughError) as ei:
+        r(xy, bad)
+    assert ei.value.code == h.EINVAL
