@@ -593,19 +593,24 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, const uint32_t* hal
     ptr += step;
     for (int ks = k0; ks < k1;) {
       const int ke = min(k1, (ks | 31) + 1);  // rows of one bitmap word
-      uint32_t bl = 0, bh = 0;                // peak flags, newest row in bit 0
+      uint32_t bl = 0, bh = 0;                // peak flags, row k in bit k & 31
 #pragma unroll 4
       for (int k = ks; k < ke; ++k) {
         const uint32_t D = __byte_perm(ptr[0], 0u, sel);
         ptr += step;
-        const uint32_t VM = vmax2(vmax2(U, C), D);
-        const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
-        const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
-        const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VU + addU, VD + 0x10000u)), TT);
-        // half of Z has bit 15 set iff C >= X there: 0x8000 - (max(X, C) - C), no borrow
-        const uint32_t Z = 0x80008000u - vmax2(X, C) + C;
-        bh = __funnelshift_l(Z, bh, 1);
-        bl = __funnelshift_l(Z << 16, bl, 1);
+        // Most rows hold no cell >= T in the warp's 60 columns: the neighbour test runs only
+        // where one does (bit 15 of a half of 0x8000 - (max(C, T) - C) is set iff C >= T).
+        const uint32_t cand = (0x80008000u - vmax2(C, TT) + C) & 0x80008000u;
+        if (__any_sync(kFull, tested && cand != 0u)) {
+          const uint32_t VM = vmax2(vmax2(U, C), D);
+          const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
+          const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
+          const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VU + addU, VD + 0x10000u)), TT);
+          // half of Z has bit 15 set iff C >= X there: 0x8000 - (max(X, C) - C), no borrow
+          const uint32_t Z = 0x80008000u - vmax2(X, C) + C;
+          bl |= ((Z >> 15) & 1u) << (k & 31);
+          bh |= (Z >> 31) << (k & 31);
+        }
         if (do_cs && tested) {
           const unsigned a0 = C & 0xffffu, a1 = C >> 16;
           if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)glo * NR + k + 1);
@@ -615,9 +620,6 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, const uint32_t* hal
         C = D;
       }
       if (tested) {
-        const int sh = 32 - (ke - ks) - (ks & 31);  // row ks to bit ks & 31
-        bl = __brev(bl) >> sh;
-        bh = __brev(bh) >> sh;
         if (bl) atomicOr(&pbits[clo * pl.nrb + (ks >> 5)], bl);
         if (bh) atomicOr(&pbits[chi * pl.nrb + (ks >> 5)], bh);
       }
@@ -716,18 +718,21 @@ __device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t*
     const unsigned long long cell0 = (unsigned long long)(j0 + c) * NR;
     for (int ws = w0; ws < w1;) {
       const int we = min(w1, (ws | 15) + 1);  // row pairs of one bitmap word
-      uint32_t bits = 0;                      // peak flags, newest row in bit 0
+      uint32_t bits = 0;                      // peak flags, row k in bit k & 31
       for (int w = ws; w < we; ++w) {
         const uint32_t N = fetch(w + 1);
-        const uint32_t U = __funnelshift_r(P, C, 16);   // rows 2w-1, 2w
-        const uint32_t D = __funnelshift_r(C, N, 16);   // rows 2w+1, 2w+2
-        const uint32_t VM = vmax2(vmax2(U, C), D);
-        const uint32_t VL = __shfl_up_sync(kFull, VM, 1);
-        const uint32_t VR = __shfl_down_sync(kFull, VM, 1);
-        const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VL + addL, VR + addR)), TT);
-        const uint32_t Z = 0x80008000u - vmax2(X, C) + C;  // bit 15 of a half: C >= X there
-        bits = __funnelshift_l(Z << 16, bits, 1);          // row 2w
-        bits = __funnelshift_l(Z, bits, 1);                // row 2w + 1
+        // the neighbour test only where some tested cell of the warp reaches T
+        const uint32_t cand = (0x80008000u - vmax2(C, TT) + C) & 0x80008000u;
+        if (__any_sync(kFull, tested && cand != 0u)) {
+          const uint32_t U = __funnelshift_r(P, C, 16);   // rows 2w-1, 2w
+          const uint32_t D = __funnelshift_r(C, N, 16);   // rows 2w+1, 2w+2
+          const uint32_t VM = vmax2(vmax2(U, C), D);
+          const uint32_t VL = __shfl_up_sync(kFull, VM, 1);
+          const uint32_t VR = __shfl_down_sync(kFull, VM, 1);
+          const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VL + addL, VR + addR)), TT);
+          const uint32_t Z = 0x80008000u - vmax2(X, C) + C;  // bit 15 of a half: C >= X there
+          bits |= (((Z >> 15) & 1u) | ((Z >> 30) & 2u)) << ((2 * w) & 31);  // rows 2w, 2w + 1
+        }
         if (do_cs && tested) {
           const unsigned a0 = C & 0xffffu, a1 = C >> 16;
           if (a0) csum += (unsigned long long)a0 * mix64(cell0 + 2 * w + 1);
@@ -736,11 +741,7 @@ __device__ void scan_packed(const Plan& pl, const uint32_t* acc, const uint32_t*
         P = C;
         C = N;
       }
-      if (tested) {
-        const int sh = 32 - 2 * (we - ws) - ((2 * ws) & 31);  // row 2 ws to bit (2 ws) & 31
-        bits = __brev(bits) >> sh;
-        if (bits) atomicOr(&pbits[c * pl.nrb + (ws >> 4)], bits);
-      }
+      if (tested && bits) atomicOr(&pbits[c * pl.nrb + (ws >> 4)], bits);
       ws = we;
     }
   }
