@@ -593,24 +593,21 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, const uint32_t* hal
     ptr += step;
     for (int ks = k0; ks < k1;) {
       const int ke = min(k1, (ks | 31) + 1);  // rows of one bitmap word
-      uint32_t bl = 0, bh = 0;                // peak flags, row k in bit k & 31
+      uint32_t bl = 0, bh = 0;                // peak flags, newest row in bit 0
+      // Branch-free: every row of this layout holds a warp's 60 cells, and skipping rows
+      // without a candidate costs more in lost overlap than it saves here.
 #pragma unroll 4
       for (int k = ks; k < ke; ++k) {
         const uint32_t D = __byte_perm(ptr[0], 0u, sel);
         ptr += step;
-        // Most rows hold no cell >= T in the warp's 60 columns: the neighbour test runs only
-        // where one does (bit 15 of a half of 0x8000 - (max(C, T) - C) is set iff C >= T).
-        const uint32_t cand = (0x80008000u - vmax2(C, TT) + C) & 0x80008000u;
-        if (__any_sync(kFull, tested && cand != 0u)) {
-          const uint32_t VM = vmax2(vmax2(U, C), D);
-          const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
-          const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
-          const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VU + addU, VD + 0x10000u)), TT);
-          // half of Z has bit 15 set iff C >= X there: 0x8000 - (max(X, C) - C), no borrow
-          const uint32_t Z = 0x80008000u - vmax2(X, C) + C;
-          bl |= ((Z >> 15) & 1u) << (k & 31);
-          bh |= (Z >> 31) << (k & 31);
-        }
+        const uint32_t VM = vmax2(vmax2(U, C), D);
+        const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
+        const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
+        const uint32_t X = vmax2(vmax2(vmax2(U + 0x00010001u, D), vmax2(VU + addU, VD + 0x10000u)), TT);
+        // half of Z has bit 15 set iff C >= X there: 0x8000 - (max(X, C) - C), no borrow
+        const uint32_t Z = 0x80008000u - vmax2(X, C) + C;
+        bh = __funnelshift_l(Z, bh, 1);
+        bl = __funnelshift_l(Z << 16, bl, 1);
         if (do_cs && tested) {
           const unsigned a0 = C & 0xffffu, a1 = C >> 16;
           if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)glo * NR + k + 1);
@@ -620,6 +617,9 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, const uint32_t* hal
         C = D;
       }
       if (tested) {
+        const int sh = 32 - (ke - ks) - (ks & 31);  // row ks to bit ks & 31
+        bl = __brev(bl) >> sh;
+        bh = __brev(bh) >> sh;
         if (bl) atomicOr(&pbits[clo * pl.nrb + (ks >> 5)], bl);
         if (bh) atomicOr(&pbits[chi * pl.nrb + (ks >> 5)], bh);
       }
