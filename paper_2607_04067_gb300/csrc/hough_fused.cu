@@ -594,10 +594,51 @@ __device__ void scan_mp(const Plan& pl, const uint32_t* acc, const uint32_t* hal
     for (int ks = k0; ks < k1;) {
       const int ke = min(k1, (ks | 31) + 1);  // rows of one bitmap word
       uint32_t bl = 0, bh = 0;                // peak flags, newest row in bit 0
-      // Branch-free: every row of this layout holds a warp's 60 cells, and skipping rows
-      // without a candidate costs more in lost overlap than it saves here.
+      int k = ks;
+      // Groups of four rows: the loads and the candidate test run straight through, and the
+      // neighbour test only for a group where some tested cell reaches T (bit 15 of a half of
+      // 0x8000 - (max(C, T) - C) is set iff C >= T); most groups have none.
+      for (; k + 4 <= ke; k += 4) {
+        uint32_t R4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          R4[i] = __byte_perm(ptr[0], 0u, sel);
+          ptr += step;
+        }
+        const uint32_t c1 = R4[0], c2 = R4[1], c3 = R4[2];
+        const uint32_t cand = ((0x80008000u - vmax2(C, TT) + C) | (0x80008000u - vmax2(c1, TT) + c1) |
+                               (0x80008000u - vmax2(c2, TT) + c2) | (0x80008000u - vmax2(c3, TT) + c3)) &
+                              0x80008000u;
+        if (__any_sync(kFull, tested && cand != 0u)) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t Cc = i == 0 ? C : R4[i - 1], Uu = i == 0 ? U : (i == 1 ? C : R4[i - 2]), Dd = R4[i];
+            const uint32_t VM = vmax2(vmax2(Uu, Cc), Dd);
+            const uint32_t VU = __shfl_up_sync(kFull, VM, 1);
+            const uint32_t VD = __shfl_down_sync(kFull, VM, 1);
+            const uint32_t X = vmax2(vmax2(vmax2(Uu + 0x00010001u, Dd), vmax2(VU + addU, VD + 0x10000u)), TT);
+            const uint32_t Z = 0x80008000u - vmax2(X, Cc) + Cc;
+            bh = __funnelshift_l(Z, bh, 1);
+            bl = __funnelshift_l(Z << 16, bl, 1);
+          }
+        } else {
+          bh <<= 4;
+          bl <<= 4;
+        }
+        if (do_cs && tested) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t Cc = i == 0 ? C : R4[i - 1];
+            const unsigned a0 = Cc & 0xffffu, a1 = Cc >> 16;
+            if (a0) csum += (unsigned long long)a0 * mix64((unsigned long long)glo * NR + k + i + 1);
+            if (a1) csum += (unsigned long long)a1 * mix64((unsigned long long)ghi * NR + k + i + 1);
+          }
+        }
+        U = R4[2];
+        C = R4[3];
+      }
 #pragma unroll 4
-      for (int k = ks; k < ke; ++k) {
+      for (; k < ke; ++k) {
         const uint32_t D = __byte_perm(ptr[0], 0u, sel);
         ptr += step;
         const uint32_t VM = vmax2(vmax2(U, C), D);
