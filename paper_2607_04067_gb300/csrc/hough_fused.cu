@@ -25,7 +25,7 @@ namespace hgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSelCap = 8;  // peak columns a lane tries alone before its hit goes to a whole warp
+constexpr int kSelCap = 12;  // peak columns a lane tries alone before its hit goes to a whole warp
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
