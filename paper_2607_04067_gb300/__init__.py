@@ -290,6 +290,23 @@ def alloc_outputs(n_hits: int, n_events: int, p: Params, checksum: bool = False,
     )
 
 
+def _check_outputs(out: "Outputs", n_hits: int, n_events: int, p: Params, need_ws: bool):
+    """The C ABI sees plain pointers: check every output tensor's device, type and size here."""
+    torch = _torch()
+    need = [("npeaks", out.npeaks, torch.int32, n_events), ("peaks", out.peaks, torch.int16, n_events * p.max_peaks * 4),
+            ("mask", out.mask, torch.uint8, n_hits), ("nkept", out.nkept, torch.int32, n_events),
+            ("status", out.status, torch.int32, 4)]
+    if out.checksum is not None:
+        need.append(("checksum", out.checksum, torch.int64, n_events))
+    if need_ws:
+        need.append(("ws", out.ws, torch.uint8, workspace_size(p, n_events)))
+    for name, t, dtype, n in need:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+            raise TypeError(f"out.{name} must be a CUDA {dtype} tensor")
+        if t.numel() < n:
+            raise ValueError(f"out.{name} holds {t.numel()} elements, {n} needed")
+
+
 def run(xy, off, p: Params, out: Outputs | None = None, checksum: bool = False, batched: bool = False,
         stream=None) -> Outputs:
     """Whole path (map, rho, vote, peaks, select) in the fused kernel; ``batched`` uses the
@@ -300,6 +317,7 @@ def run(xy, off, p: Params, out: Outputs | None = None, checksum: bool = False, 
     ne = off.shape[0] - 1
     if out is None:
         out = alloc_outputs(xy.shape[0], ne, p, checksum, xy.device)
+    _check_outputs(out, xy.shape[0], ne, p, need_ws=False)
     fn = load().hough_run_batched if batched else load().hough_run
     rc = fn(_ptr(xy), xy.shape[0], _ptr(off), ne, ctypes.byref(p), _ptr(out.npeaks), _ptr(out.peaks), _ptr(out.mask),
             _ptr(out.nkept), _ptr(out.checksum), _ptr(out.ws), out.ws.numel(), _ptr(out.status), _stream(stream))
@@ -313,6 +331,7 @@ def run_static(xy, off, p: Params, out: Outputs, stream=None) -> Outputs:
     torch = _torch()
     xy = _dev(xy, "xy", torch.int32)
     off = _dev(off, "off", torch.int64)
+    _check_outputs(out, xy.shape[0], off.shape[0] - 1, p, need_ws=False)
     rc = load().hough_run_batched_static(
         _ptr(xy), xy.shape[0], _ptr(off), off.shape[0] - 1, ctypes.byref(p), _ptr(out.npeaks), _ptr(out.peaks),
         _ptr(out.mask), _ptr(out.nkept), _ptr(out.checksum), _ptr(out.status), _stream(stream))

@@ -666,7 +666,7 @@ int hough_run_batched(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off,
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e);
   g_graphs.push_front(GraphEntry{key, exec});
-  while (g_graphs.size() > 16) {
+  while (g_graphs.size() > 64) {
     cudaGraphExecDestroy(g_graphs.back().exec);
     g_graphs.pop_back();
   }
@@ -795,7 +795,12 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
     if (e != cudaSuccess) break;
     rc = hough_run_batched(d_xy + 2 * a0, nh, roff, n, p, d_npk + e0, d_pk + e0 * mp, d_mask + a0, d_nk + e0,
                            nullptr, b + L.ws, L.ws_bytes, d_status, stream);
-    if (rc) return rc;
+    if (rc) {  // nothing may still read or write the caller's host buffers after the return
+      cudaStreamSynchronize(hp.in);
+      cudaStreamSynchronize(hp.out);
+      cudaStreamSynchronize(st);
+      return rc;
+    }
     e = launch_pack_peaks(d_npk + e0, d_pk + e0 * mp, n, p->max_peaks, (long long*)(d_poff + e0 + c),
                           d_dense + e0 * mp, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev_comp, st);
@@ -829,9 +834,10 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
   h_peak_off[n_events] = base;
   int32_t flags = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, hp.out);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(hp.out);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(hp.peaks);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // every stream is drained on every exit: no copy touches the caller's buffers afterwards
+  const cudaError_t s1 = cudaStreamSynchronize(hp.in), s2 = cudaStreamSynchronize(hp.out);
+  const cudaError_t s3 = cudaStreamSynchronize(hp.peaks), s4 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = s1 != cudaSuccess ? s1 : s2 != cudaSuccess ? s2 : s3 != cudaSuccess ? s3 : s4;
   if (e != cudaSuccess) return cuda_fail(e);
   if (over) return HOUGH_EWORKSPACE;
   return flags ? HOUGH_EDEVICE : HOUGH_OK;

@@ -361,6 +361,15 @@ def test_host_errors(h):
     with pytest.raises(h.HoughError) as ei:
         h.run_static(xy, off, p, out)
     assert ei.value.code == h.EINVAL
+    # output tensors too small or of the wrong type are refused before anything is enqueued
+    out = h.alloc_outputs(4, 1, p)
+    out.peaks = out.peaks[:, :10]
+    with pytest.raises(ValueError):
+        h.run(xy, off, p, out=out)
+    out = h.alloc_outputs(4, 1, p)
+    out.mask = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(TypeError):
+        h.run(xy, off, p, out=out, batched=True)
 
 
 # ---------------------------------------------------------------- Eq. (2) circle recovery
