@@ -74,7 +74,8 @@ static int round16(int x) { return (x + 15) & ~15; }
 static bool layout(Plan& pl) {
   const int wpad = pl.groups * 32;
   const int cell = pl.acc32 ? 4 : 2;
-  const int acc_bytes = pl.mp ? (pl.tile_w / 2) * pl.rows_phys * 4 : wpad * pl.nrho_pad * cell;
+  // mirror-pair: groups / 2 word groups of 32 lanes (the last may be part idle) x rows_phys
+  const int acc_bytes = pl.mp ? (pl.groups / 2) * 32 * pl.rows_phys * 4 : wpad * pl.nrho_pad * cell;
   const int sel_bytes = (2 * pl.n_theta + 64) * 4 + pl.n_theta * 16 + pl.n_theta * pl.nrb_g * 4;
   int o = 0;
   pl.off_acc = o;
@@ -168,16 +169,37 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
     pl.fp_dhi = (float)(-delta - 0.5);
   }
   const int cell_choice = acc32 < 0 ? 0 : acc32;
+  // Mirror pairs (columns j and N-1-j in one word) need an even N_theta and a table with
+  // c[N-1-j] = -c[j], s[N-1-j] = s[j] (true for round-half-away-from-zero), int16 cells and
+  // the float row estimate.
+  bool sym = false;
+  if (p->n_theta % 2 == 0 && !cell_choice && pl.fpbin) {
+    TrigTable tt;
+    host_trig(p->n_theta, &tt);
+    sym = true;
+    for (int j = 0; j < p->n_theta && sym; ++j)
+      sym = tt.c[p->n_theta - 1 - j] == -tt.c[j] && tt.s[p->n_theta - 1 - j] == tt.s[j];
+  }
   for (int T = (p->theta_tiles ? p->theta_tiles : 1); T <= (p->theta_tiles ? p->theta_tiles : 64); ++T) {
     if (p->peak_mode == HOUGH_PEAK_ITERATIVE && T > 1) {
       if (p->theta_tiles) return HOUGH_EPARAM;  // the iterative finder needs the whole accumulator
       break;
     }
-    const int W = (p->n_theta + T - 1) / T;
-    if ((T - 1) * W >= p->n_theta) continue;  // every tile must own at least one column
+    // A mirror-pair tile owns WD = ceil(N/2 / T) words (columns [a, a + WD) and their mirrors;
+    // the last tile fewer), in word groups of 32 lanes; other tiles W = ceil(N / T) columns.
+    int W;
+    if (sym) {
+      const int NW = p->n_theta / 2, WD = (NW + T - 1) / T;
+      if ((T - 1) * WD >= NW) continue;  // every tile must own at least one word
+      W = 2 * WD;
+      pl.groups = 2 * ((WD + 31) / 32);
+    } else {
+      W = (p->n_theta + T - 1) / T;
+      if ((T - 1) * W >= p->n_theta) continue;  // every tile must own at least one column
+      pl.groups = (W + 31) / 32;
+    }
     pl.tiles = T;
     pl.tile_w = W;
-    pl.groups = (W + 31) / 32;
     pl.acc32 = cell_choice;
     pl.nrho_pad = pl.acc32 ? p->n_rho : ((p->n_rho + 1) & ~1);
     const int halo = T > 1 ? 32 : 0;
@@ -200,20 +222,8 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       if (p->theta_tiles) return HOUGH_EPARAM;
       continue;
     }
-    // Mirror pairs need whole 64-column group pairs per tile (a tile then owns words
-    // [t W/2, (t+1) W/2): columns and their mirrors), a table with c[N-1-j] = -c[j],
-    // s[N-1-j] = s[j] (true for round-half-away-from-zero), and, across tiles, the
-    // mirror-pair layout itself (int16 cells, float row estimate).
-    pl.mirror = 0;
-    if (p->n_theta % (64 * T) == 0 && (T == 1 || (!pl.acc32 && pl.fpbin))) {
-      TrigTable tt;
-      host_trig(p->n_theta, &tt);
-      bool sym = true;
-      for (int j = 0; j < p->n_theta && sym; ++j)
-        sym = tt.c[p->n_theta - 1 - j] == -tt.c[j] && tt.s[p->n_theta - 1 - j] == tt.s[j];
-      pl.mirror = sym ? 1 : 0;
-    }
-    pl.mp = pl.mirror && !pl.acc32 && pl.fpbin;
+    pl.mirror = sym ? 1 : 0;
+    pl.mp = pl.mirror;
     if (pl.mp) mp_consts(pl, p->n_rho);
     // row ranges of the peak scan: the power of two that minimises the slowest warp's row
     // steps, each unit (30 columns x one range) paying two extra rows to prime its window

@@ -453,6 +453,7 @@ __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, con
     return;
   }
   const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
+  if (!L.on) return;
   const float c0 = pl.mp_c0;
   const uint32_t base = L.col1, base2 = L.col1 - (uint32_t)pl.mp_k7;
   const float4* hb4 = reinterpret_cast<const float4*>(hb);
@@ -502,6 +503,7 @@ __device__ __forceinline__ void vote_mp64(const Plan& pl, const VoteLane& L, con
     }
     return;
   }
+  if (!L.on) return;
   for (int q = L.p; q < nv; q += L.P) {
     const longlong2 h = hw[q];
     const long long vs = h.y * sj + kH, uc = h.x * cj;
@@ -1163,7 +1165,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   const int wpad = pl.groups * 32;
   const int rows_w = A32 ? nrp : (nrp >> 1);  // words per column
   // mirror-pair tiles: words [aw, aw + Wd), i.e. columns [aw, aw + Wd) and their mirrors
-  const int Wd = pl.mp ? (wt >> 1) : 0, aw = t * Wd;
+  // (full tiles own tile_w / 2 words, the last one possibly fewer)
+  const int Wd = pl.mp ? (wt >> 1) : 0, aw = t * (pl.tile_w >> 1);
 
   // lane roles of the vote
   VoteLane L;
@@ -1199,9 +1202,11 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     L.p = warp % P2;
     L.P = P2;
     const int c1 = gpair * 32 + lane;
-    L.on = true;
-    L.cj = tc[(pl.mp ? aw : j0) + c1];
-    L.sj = ts[(pl.mp ? aw : j0) + c1];
+    L.on = !pl.mp || c1 < Wd;  // lanes past the tile's last word idle
+    if (L.on) {
+      L.cj = tc[(pl.mp ? aw : j0) + c1];
+      L.sj = ts[(pl.mp ? aw : j0) + c1];
+    }
     if (pl.mp) {
       L.col1 = acc_s + (uint32_t)mp_word(c1, 0, pl.rows_phys) * 4u;
     } else {
