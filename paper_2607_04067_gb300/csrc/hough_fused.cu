@@ -132,13 +132,16 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
 __device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn, int2* hb, int* s_nv, int* s_flags,
                              bool as_float, long long lsq, uint16_t* idx) {
   const int lane = threadIdx.x & 31;
+  // each thread's next hit is loaded one pass ahead, so the loads overlap the mapping
+  int2 hn = threadIdx.x < cn ? xy[base + threadIdx.x] : make_int2(0, 0);
   for (int i0 = 0; i0 < cn; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
+    const int2 h = hn;
+    if (i + (int)blockDim.x < cn) hn = xy[base + i + blockDim.x];
     long long u = 0, v = 0;
     int st = 0;
     bool ok = false;
     if (i < cn) {
-      const int2 h = xy[base + i];
       st = map_hit(h.x, h.y, u, v);
       ok = (st == 0);
     }
