@@ -43,10 +43,13 @@ def serve_events(h, srv, ev, ids, maxp):
     return out
 
 
-def test_serve_matches_batched_path(h):
+@pytest.mark.parametrize("iterative", [False, True])
+def test_serve_matches_batched_path(h, iterative):
     cfg = gen.CONFIGS["served"]
     ev = gen.generate(cfg, 300)
     p = cfg_params(h, cfg)
+    if iterative:  # the paper's iterative peak finder through the serving loop
+        p.peak_mode, p.rel_num, p.rel_den, p.nms_radius = h.PEAK_ITERATIVE, 1, 2, 3
     ref = h.run(torch.from_numpy(ev.xy).cuda(), torch.from_numpy(ev.off).cuda(), p, batched=True)
     npk, nk, mk, pk = to_np(ref.npeaks), to_np(ref.nkept), to_np(ref.mask), peaks_np(ref.peaks)
     with h.Server(p, slots=3, max_batch_events=40, flush_us=100) as srv:
