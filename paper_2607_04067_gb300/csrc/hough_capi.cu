@@ -87,8 +87,16 @@ static bool layout(Plan& pl) {
   o += round16(pl.hit_cap * 8);
   pl.off_idx = o;
   if (pl.mp) o += round16(pl.hit_cap * 2);
-  pl.off_pbits = o;
-  o += round16(wpad * pl.nrb * 4);
+  pl.off_pbits = o;  // also the iterative finder's slice and column maxima
+  {
+    int iter_words = 0;
+    if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
+      const int sorted_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 31) / 32;
+      iter_words = iter_scratch_words(pl.n_theta, pl.n_rho, kIterSliceRows);
+      if (pl.iter_cap > 0 && sorted_words > iter_words) iter_words = sorted_words;
+    }
+    o += round16((wpad * pl.nrb > iter_words ? wpad * pl.nrb : iter_words) * 4);
+  }
   pl.off_cnt = o;
   o += round16(wpad * pl.key_groups * 4);
   pl.off_unres = o;
@@ -260,9 +268,14 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       pl.key_shift = ks;
       pl.key_words = gw;
     }
+    // the most staged hits, then (iterative finder) the most candidate keys of its sorted form
     for (int cap = 4096; cap >= 512; cap >>= 1) {
       pl.hit_cap = cap;
-      if (layout(pl)) return HOUGH_OK;
+      const int icap0 = pl.peak_mode == HOUGH_PEAK_ITERATIVE ? 8192 : 0;
+      for (int icap = icap0; icap >= 0; icap = icap > 1024 ? icap / 2 : icap - 1024) {
+        pl.iter_cap = icap;
+        if (layout(pl)) return HOUGH_OK;
+      }
     }
     if (p->theta_tiles) return HOUGH_ESMEM;
   }

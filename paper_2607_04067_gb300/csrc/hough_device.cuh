@@ -99,103 +99,327 @@ __device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// Iterative peak extraction (the paper's finder, Sec. 2) over an accumulator behind `cells`
-// (get(j, k) -> votes of a cell not yet suppressed, 0 once suppressed; clear(j, k) suppresses).
-// cm: n_theta words of shared scratch holding each column's best cell packed as
-// (votes << 16) | (n_rho - 1 - k): within a column the larger word is the cell with more votes
-// and, on equal votes, the smaller k. s: 2 ints of shared scratch. Each pass: warp 0 takes the
-// column with the most votes (equal votes: the smaller column, i.e. raster order); if that cell
-// qualifies it is the next peak, the whole CTA clears its window and warps re-scan the 2R + 1
-// columns it touches, one column per warp. Every pass clears the extracted cell, so the loop
-// ends. Records go to dst in extraction order (the first max_peaks); returns the true count.
+// Words of shared scratch the per-pass iterative finder takes (extract_iterative_passes's cm)
+// for an n_theta x n_rho accumulator in slices of SH rows: an odd-padded stride of slice maxima
+// per column, and one word per column.
+__host__ __device__ inline int iter_slice_stride(int NR, int SH) { return ((NR + SH - 1) / SH) | 1; }
+__host__ __device__ inline int iter_scratch_words(int NT, int NR, int SH) {
+  return NT * iter_slice_stride(NR, SH) + NT;
+}
+
+// Iterative peak extraction (the paper's finder, Sec. 2), one pass per peak, over an
+// accumulator behind `cells` (get(j, k) -> votes of a cell not yet suppressed, 0 once
+// suppressed; clear(j, k) suppresses one cell without touching any other cell's value, so that
+// other lanes may read and clear other cells meanwhile). The general form of the finder, taken
+// when the sorted form below does not apply.
+// Cells are ordered by the packed word (votes << 16) | (n_rho - 1 - k): within a column the
+// larger word is the cell with more votes and, on equal votes, the smaller k. Across columns
+// the key (votes << 16) | (0xffff - j) orders by votes and, on equal votes, the smaller column
+// (raster order). cm: iter_scratch_words(NT, NR, SH) words of shared scratch: the best packed
+// word of every slice of SH rows (a power of two, at least 32) of every column (stride
+// iter_slice_stride), then of every column. s: 1 int of shared scratch.
+// The CTA builds the maxima; then warp 0 alone runs the passes, with no block barrier. Each
+// pass takes the best column key; if that cell qualifies it is the next peak, its window is
+// cleared, and the slices the window touches are re-scanned by groups of lanes, without the
+// rows being cleared (they hold no votes any more, and a cell without votes never qualifies,
+// since thr >= 1); then groups of lanes rebuild the window's column words. Every pass clears
+// the extracted cell, so the loop ends. Records go to dst in extraction order (the first
+// max_peaks); returns the true count.
 template <class Cells>
-__device__ int extract_iterative(Cells& cells, int NT, int NR, int thr, int rel_num, int rel_den, int R, int maxp,
-                                 uint32_t* cm, hough_peak* dst, int* s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  auto column_best = [&](int j) {
+__device__ int extract_iterative_passes(Cells& cells, int NT, int NR, int SH, int thr, int rel_num, int rel_den,
+                                        int R, int maxp, uint32_t* cm, hough_peak* dst, int* s) {
+  const int lane = threadIdx.x & 31, bd = blockDim.x;
+  const int NS = (NR + SH - 1) / SH, NSP = iter_slice_stride(NR, SH);
+  uint32_t* sl = cm;
+  uint32_t* col = cm + NT * NSP;
+  auto wrap = [&](int jj) { return jj < 0 ? jj + NT : (jj >= NT ? jj - NT : jj); };
+  auto pack = [&](int j, int k) { return ((uint32_t)cells.get(j, k) << 16) | (uint32_t)(NR - 1 - k); };
+  // slice maxima (a warp's lanes take consecutive columns of one slice), then column words
+  for (int it = threadIdx.x; it < NT * NS; it += bd) {
+    const int j = it % NT, q = it / NT;
+    const int kb = min(NR, (q + 1) * SH);
     uint32_t b = 0;
-    for (int k = lane; k < NR; k += 32) {
-      const uint32_t v = (uint32_t)cells.get(j, k);
-      b = max(b, (v << 16) | (uint32_t)(NR - 1 - k));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
-    return b;
-  };
-  for (int j = warp; j < NT; j += nwarps) {
-    const uint32_t b = column_best(j);
-    if (lane == 0) cm[j] = b;
+#pragma unroll 8
+    for (int k = q * SH; k < kb; ++k) b = max(b, pack(j, k));
+    sl[j * NSP + q] = b;
   }
   __syncthreads();
-  long long amax = 0;
-  {
+  for (int j = threadIdx.x; j < NT; j += bd) {
     uint32_t m = 0;
-    for (int j = lane; j < NT; j += 32) m = max(m, cm[j] >> 16);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    amax = m;  // every warp computes the same maximum
+    for (int q = 0; q < NS; ++q) m = max(m, sl[j * NSP + q]);
+    col[j] = m;
   }
-  const int W = 2 * R + 1;
-  int n = 0;
-  for (;;) {
-    if (warp == 0) {
-      uint32_t bv = 0;
-      int bj = NT;
-      for (int j = lane; j < NT; j += 32) {
-        const uint32_t c = cm[j];
-        if ((c >> 16) > (bv >> 16) || bj == NT) {
-          bv = c;
-          bj = j;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    auto best_key = [&]() {
+      uint32_t b = 0;
+#pragma unroll 8
+      for (int j = lane; j < NT; j += 32) b = max(b, (col[j] & 0xffff0000u) | (uint32_t)(0xffff - j));
+      return __reduce_max_sync(0xffffffffu, b);
+    };
+    auto log2_floor = [](int x) { return 31 - __clz(x); };
+    const long long amax = (long long)(best_key() >> 16);
+    // every per-pass index below is a shift or a multiply: SH is a power of two, lane groups
+    // are powers of two, and item / W = (item * mW) >> 21, exact for W <= 129, item < 8192
+    const int W = 2 * R + 1, LSH = log2_floor(SH);
+    const uint32_t mW = ((1u << 21) + W - 1) / W;
+    const int L1 = log2_floor(max(1, 32 / W));  // log2 lanes per window column
+    int n = 0;
+    for (;;) {
+      const uint32_t best = best_key();
+      const int v = (int)(best >> 16), j = 0xffff - (int)(best & 0xffffu);
+      // thr >= 1, so a qualifying cell has a key and j is a column (ok is warp-uniform)
+      if (!(v >= thr && (long long)v * rel_den >= (long long)rel_num * amax)) break;
+      const int k = NR - 1 - (int)(col[j] & 0xffffu);
+      if (lane == 0 && n < maxp) {
+        hough_peak pk;
+        pk.theta_bin = (int16_t)j;
+        pk.rho_bin = (int16_t)k;
+        pk.votes = (int16_t)v;
+        pk.flags = 0;
+        dst[n] = pk;
+      }
+      ++n;
+      // the window: columns j - R .. j + R and rows r0 .. r1; a column past either end of the
+      // theta range is taken from the other end with the rows mirrored
+      const int r0 = max(0, k - R), r1 = min(NR - 1, k + R);
+      for (int a = lane; a < W; a += 32) {  // clear: a lane per window column
+        int jj = j - R + a, c0 = r0, c1 = r1;
+        if (jj < 0 || jj >= NT) {
+          jj = wrap(jj);
+          c0 = NR - 1 - r1;
+          c1 = NR - 1 - r0;
+        }
+        for (int kk = c0; kk <= c1; ++kk) cells.clear(jj, kk);
+      }
+      // re-scan the touched slices: item (q, a) is window column a, its q-th touched slice,
+      // taken by a group of 2^LP lanes, each over SH >> LP rows
+      const int span = max((r1 >> LSH) - (r0 >> LSH), ((NR - 1 - r0) >> LSH) - ((NR - 1 - r1) >> LSH)) + 1;
+      const int cnt = span * W, LP = max(0, L1 - (span - 1)), RP = SH >> LP;
+      for (int base = 0; base < cnt; base += 32 >> LP) {
+        const int item = base + (lane >> LP), part = lane & ((1 << LP) - 1);
+        uint32_t b = 0;
+        int qs = -1, jj = 0;
+        if (item < cnt) {
+          const int q = (int)(((uint32_t)item * mW) >> 21), a = item - q * W;
+          int x0 = r0, x1 = r1;
+          jj = j - R + a;
+          if (jj < 0 || jj >= NT) {
+            jj = wrap(jj);
+            x0 = NR - 1 - r1;
+            x1 = NR - 1 - r0;
+          }
+          qs = (x0 >> LSH) + q;
+          if (qs <= (x1 >> LSH)) {
+            const int ka = (qs << LSH) + part * RP;
+#pragma unroll 8
+            for (int t = 0; t < RP; ++t) {
+              const int kk = ka + t;
+              if (kk < NR) {
+                const uint32_t w = pack(jj, kk);
+                if (kk < x0 || kk > x1) b = max(b, w);
+              }
+            }
+          } else {
+            qs = -1;
+          }
+        }
+        for (int o = 1; o < (1 << LP); o <<= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        if (part == 0 && qs >= 0) sl[jj * NSP + qs] = b;
+      }
+      __syncwarp();
+      // the window's column words, 2^L1 lanes per column
+      for (int base = 0; base < W; base += 32 >> L1) {
+        const int a = base + (lane >> L1), part = lane & ((1 << L1) - 1);
+        uint32_t m = 0;
+        int jj = 0;
+        if (a < W) {
+          jj = wrap(j - R + a);
+#pragma unroll 4
+          for (int q = part; q < NS; q += 1 << L1) m = max(m, sl[jj * NSP + q]);
+        }
+        for (int o = 1; o < (1 << L1); o <<= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (part == 0 && a < W) col[jj] = m;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) s[0] = n;
+  }
+  __syncthreads();
+  const int n = s[0];
+  __syncthreads();
+  return n;
+}
+
+// Cell (j, k) lies in the suppression window of (ji, ki): columns ji - R .. ji + R and rows
+// ki - R .. ki + R, a column past either end of the theta range taken from the other end with
+// the rows mirrored (2R < n_theta, so at most one of the three column cases holds).
+__device__ __forceinline__ bool in_window(int ji, int ki, int j, int k, int NT, int NR, int R) {
+  const int d = j - ji;
+  if (d >= -R && d <= R) return abs(k - ki) <= R;
+  if (d - NT >= -R || d + NT <= R) return abs(NR - 1 - k - ki) <= R;
+  return false;
+}
+
+// Sets bits b0 .. b1 of a shared bitmap.
+__device__ __forceinline__ void or_bits(uint32_t* bm, int b0, int b1) {
+  const int w0 = b0 >> 5, w1 = b1 >> 5;
+  for (int w = w0; w <= w1; ++w) {
+    uint32_t m = 0xffffffffu;
+    if (w == w0) m &= 0xffffffffu << (b0 & 31);
+    if (w == w1) m &= 0xffffffffu >> (31 - (b1 & 31));
+    atomicOr(&bm[w], m);
+  }
+}
+
+// The iterative finder (Sec. 2) in sorted form. Taking the unsuppressed cell with the most votes
+// (raster order on ties) and suppressing its window, until the best cell fails the threshold, is
+// the same as walking the cells that pass the threshold in that order and keeping each one that
+// no window kept so far covers: every cell ranked above the next peak is a peak or lies in a
+// kept window, so the first uncovered candidate is the cell the one-pass-per-peak form takes.
+// Candidates are cells with votes >= max(thr, ceil(rel_num * amax / rel_den)), keyed
+// (votes << 20) | ((1023 - j) << 10) | (1023 - k), so that the larger key comes first.
+// keys: cap words, sup: a zeroed bitmap of n_theta * n_rho bits (cell (j, k) is bit j NR + k),
+// both shared. The CTA finds the maximum, collects and sorts the keys (bitonic); warp 0 walks
+// them 32 at a time: lanes drop candidates covered by earlier chunks' windows, then the lowest
+// remaining lane is kept and the lanes its window covers drop out, until none remain; the
+// kept windows go into the bitmap for the next chunks.
+// Returns the true count, or -1 (written nothing) when the maximum exceeds 4095 votes or the
+// candidates exceed cap: those take the per-pass form. s: 2 ints of shared scratch.
+template <class Cells>
+__device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, int rel_num, int rel_den, int R,
+                                        int maxp, uint32_t* keys, int cap, uint32_t* sup, hough_peak* dst, int* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, bd = blockDim.x;
+  if (threadIdx.x == 0) {
+    s[0] = 0;
+    s[1] = 0;
+  }
+  __syncthreads();
+  // the maximum (a warp takes rows, its lanes consecutive columns)
+  {
+    int m = 0;
+    for (int k = warp; k < NR; k += nwarps)
+      for (int j = lane; j < NT; j += 32) m = max(m, cells.get(j, k));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0 && m) atomicMax(&s[0], m);
+  }
+  __syncthreads();
+  const int amax = s[0];
+  if (amax > 4095) return -1;  // uniform: every thread read the same value
+  const long long need = ((long long)rel_num * amax + rel_den - 1) / rel_den;
+  const int tq = (int)max((long long)thr, need);
+  // the candidates, in any order; the count may exceed cap (then only counted)
+  for (int k = warp; k < NR; k += nwarps) {
+    for (int j0 = 0; j0 < NT; j0 += 32) {
+      const int j = j0 + lane;
+      const int v = j < NT ? cells.get(j, k) : 0;
+      const bool c = v >= tq;
+      const uint32_t bal = __ballot_sync(0xffffffffu, c);
+      if (bal) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s[1], __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+        if (c && pos < cap) keys[pos] = ((uint32_t)v << 20) | ((uint32_t)(1023 - j) << 10) | (uint32_t)(1023 - k);
+      }
+    }
+  }
+  __syncthreads();
+  const int C = s[1];
+  if (C > cap) return -1;
+  int N = 32;
+  while (N < C) N <<= 1;
+  for (int i = C + threadIdx.x; i < N; i += bd) keys[i] = 0u;
+  const int nbits = NT * NR;
+  for (int i = threadIdx.x; i < (nbits + 31) >> 5; i += bd) sup[i] = 0u;
+  __syncthreads();
+  // bitonic sort, descending
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < (N >> 1); t += bd) {
+        const int i = 2 * t - (t & (stride - 1)), l = i + stride;
+        const uint32_t a = keys[i], b = keys[l];
+        if (((i & size) == 0) == (a < b)) {
+          keys[i] = b;
+          keys[l] = a;
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const uint32_t ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if ((ov >> 16) > (bv >> 16) || ((ov >> 16) == (bv >> 16) && oj < bj)) {
-          bv = ov;
-          bj = oj;
-        }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < 32) {
+    const int W = 2 * R + 1;
+    const uint32_t mW = ((1u << 21) + W - 1) / W;  // item / W = (item * mW) >> 21, exact here
+    int n = 0;
+    for (int base = 0; base < C; base += 32) {
+      const int idx = base + lane;
+      const uint32_t key = keys[idx];  // idx < N: zero past C
+      const int v = (int)(key >> 20), j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+      const int cb = j * NR + k;
+      const bool live = idx < C && !((sup[cb >> 5] >> (cb & 31)) & 1u);
+      uint32_t L = __ballot_sync(0xffffffffu, live), A = 0;
+      const int jk = (j << 16) | k;
+      while (L) {
+        const int i = __ffs(L) - 1;
+        const int ji = __shfl_sync(0xffffffffu, jk, i);
+        A |= 1u << i;
+        L &= ~__ballot_sync(0xffffffffu, in_window(ji >> 16, ji & 0xffff, j, k, NT, NR, R));
       }
-      const int v = (int)(bv >> 16);
-      const bool ok = bj < NT && v >= thr && (long long)v * rel_den >= (long long)rel_num * amax;
-      if (lane == 0) {
-        s[0] = ok ? bj : -1;
-        s[1] = ok ? NR - 1 - (int)(bv & 0xffffu) : 0;
-        if (ok && n < maxp) {
+      const int na = __popc(A);
+      if (na) {
+        const bool kept = (A >> lane) & 1u;
+        const int r = __popc(A & ((1u << lane) - 1u));
+        if (kept && n + r < maxp) {
           hough_peak pk;
-          pk.theta_bin = (int16_t)bj;
-          pk.rho_bin = (int16_t)(NR - 1 - (int)(bv & 0xffffu));
+          pk.theta_bin = (int16_t)j;
+          pk.rho_bin = (int16_t)k;
           pk.votes = (int16_t)v;
           pk.flags = 0;
-          dst[n] = pk;
+          dst[n + r] = pk;
         }
+        // this chunk's keys are in registers now: its words hold the kept cells
+        __syncwarp();
+        if (kept) keys[base + r] = (uint32_t)jk;
+        __syncwarp();
+        for (int it = lane; it < na * W; it += 32) {
+          const int p = (int)(((uint32_t)it * mW) >> 21), a = it - p * W;
+          const uint32_t c = keys[base + p];
+          const int jp = (int)(c >> 16), kp = (int)(c & 0xffffu);
+          int jj = jp - R + a, x0 = max(0, kp - R), x1 = min(NR - 1, kp + R);
+          if (jj < 0 || jj >= NT) {
+            jj = jj < 0 ? jj + NT : jj - NT;
+            const int t0 = NR - 1 - x1;
+            x1 = NR - 1 - x0;
+            x0 = t0;
+          }
+          or_bits(sup, jj * NR + x0, jj * NR + x1);
+        }
+        __syncwarp();
+        n += na;
       }
     }
-    __syncthreads();
-    const int j = s[0], k = s[1];
-    if (j < 0) break;
-    ++n;
-    for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
-      const int dj = i / W - R, dk = i % W - R;
-      int jj = j + dj, kk = k + dk;
-      if (kk < 0 || kk >= NR) continue;
-      if (jj < 0 || jj >= NT) {
-        jj = jj < 0 ? jj + NT : jj - NT;
-        kk = NR - 1 - kk;
-      }
-      cells.clear(jj, kk);
-    }
-    __syncthreads();
-    for (int dj = warp - R; dj <= R; dj += nwarps) {
-      int jj = j + dj;
-      jj = jj < 0 ? jj + NT : (jj >= NT ? jj - NT : jj);
-      const uint32_t b = column_best(jj);
-      if (lane == 0) cm[jj] = b;
-    }
-    __syncthreads();
+    if (lane == 0) s[0] = n;
   }
+  __syncthreads();
+  const int n = s[0];
+  __syncthreads();
   return n;
+}
+
+// The iterative finder: the sorted form where it applies (cap > 0), else one pass per peak.
+// scratch: shared words for both forms, which never run at the same time:
+// max(iter_scratch_words(NT, NR, SH), cap + ceil(NT NR / 32)) when sup is null (the sorted
+// form's bitmap then follows its cap keys), else max(iter_scratch_words(NT, NR, SH), cap) with
+// sup a shared bitmap of NT NR bits that the sorted form may use (and leaves set).
+template <class Cells>
+__device__ int extract_iterative(Cells& cells, int NT, int NR, int SH, int thr, int rel_num, int rel_den, int R,
+                                 int maxp, uint32_t* scratch, int cap, uint32_t* sup, hough_peak* dst, int* s) {
+  if (cap > 0) {
+    const int n = extract_iterative_sorted(cells, NT, NR, thr, rel_num, rel_den, R, maxp, scratch, cap,
+                                           sup ? sup : scratch + cap, dst, s);
+    if (n >= 0) return n;
+  }
+  return extract_iterative_passes(cells, NT, NR, SH, thr, rel_num, rel_den, R, maxp, scratch, dst, s);
 }
 
 __device__ __forceinline__ void flag_status(int* status, int f) {

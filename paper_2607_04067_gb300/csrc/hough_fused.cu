@@ -384,23 +384,29 @@ __device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, int Wd,
   return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
 }
 
-// Cells of the CTA's accumulator for the iterative finder (one tile): read, and suppress by
-// clearing the cell's half of its word (or the word, with int32 cells).
-template <bool A32>
+// Cells of the CTA's accumulator for the iterative finder (one tile): read, and suppress by a
+// 16-bit store of zero into the cell's half of its word (a 32-bit store with int32 cells), which
+// leaves the other half of the word alone.
+template <bool A32, bool MP>
 struct FusedCells {
   uint32_t* acc;
-  int Wd, nrp;
-  bool mp;
-  const Plan* pl;
-  __device__ int get(int j, int k) const { return mp ? mp_get(acc, j, k, Wd, *pl) : acc_get<A32>(acc, j, k, nrp); }
-  __device__ void clear(int j, int k) {
-    if (mp) {
+  int Wd, nrp, rp;  // tile words, padded rows (other layouts), rows with guards (mirror-pair)
+  __device__ int get(int j, int k) const {
+    if (MP) {
       const bool hi = j >= Wd;
-      atomicAnd(&acc[mp_word(hi ? 2 * Wd - 1 - j : j, k + 1, pl->rows_phys)], hi ? 0x0000ffffu : 0xffff0000u);
+      const uint32_t x = acc[mp_word(hi ? 2 * Wd - 1 - j : j, k + 1, rp)];
+      return hi ? (int)(x >> 16) : (int)(x & 0xffffu);
+    }
+    return acc_get<A32>(acc, j, k, nrp);
+  }
+  __device__ void clear(int j, int k) {
+    if (MP) {
+      const bool hi = j >= Wd;
+      reinterpret_cast<uint16_t*>(acc)[2 * mp_word(hi ? 2 * Wd - 1 - j : j, k + 1, rp) + (hi ? 1 : 0)] = 0;
     } else if (A32) {
       acc[acc_index<true>(j, k, nrp)] = 0u;
     } else {
-      atomicAnd(&acc[acc_index<false>(j, k, nrp)], (k & 1) ? 0x0000ffffu : 0xffff0000u);
+      reinterpret_cast<uint16_t*>(acc)[2 * acc_index<false>(j, k, nrp) + (k & 1)] = 0;
     }
   }
 };
@@ -1294,18 +1300,21 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       mp_fold(pl, acc, Wd, nullptr);
       __syncthreads();
     }
-    FusedCells<A32> cells{acc, Wd, nrp, pl.mp != 0, &pl};
-    if (do_cs) {
-      unsigned long long cs = 0;
-      for (int c = tid; c < NT * NR; c += bd) {
-        const int v = cells.get(c / NR, c % NR);
-        if (v) cs += (unsigned long long)v * mix64((unsigned long long)c + 1);
+    auto iterative = [&](auto cells) {
+      if (do_cs) {
+        unsigned long long cs = 0;
+        for (int c = tid; c < NT * NR; c += bd) {
+          const int v = cells.get(c / NR, c % NR);
+          if (v) cs += (unsigned long long)v * mix64((unsigned long long)c + 1);
+        }
+        cs_tile = block_sum_u64(cs, sh.red);
       }
-      cs_tile = block_sum_u64(cs, sh.red);
-    }
-    __syncthreads();
-    total = extract_iterative(cells, NT, NR, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius, maxp, pbits,
-                              io.peaks + e * (long long)maxp, sh.tmp);
+      __syncthreads();
+      return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
+                               maxp, pbits, pl.iter_cap, nullptr, io.peaks + e * (long long)maxp, sh.tmp);
+    };
+    total = pl.mp ? iterative(FusedCells<A32, true>{acc, Wd, nrp, pl.rows_phys})
+                  : iterative(FusedCells<A32, false>{acc, Wd, nrp, pl.rows_phys});
     n_low = total;
   } else {
     // 3. peak scan

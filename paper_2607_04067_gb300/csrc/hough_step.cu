@@ -310,18 +310,22 @@ struct GlobalCells {
   }
 };
 
-__global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, int NR, int thr, int rel_num,
-                                       int rel_den, int R, int maxp, int* npeaks, hough_peak* peaks, int* status) {
+__global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, int NR, int SH, int cap, int thr,
+                                       int rel_num, int rel_den, int R, int maxp, int* npeaks, hough_peak* peaks,
+                                       int* status) {
   extern __shared__ uint32_t sm[];
   __shared__ int s_sel[2];
   const long long e = blockIdx.x;
+  // the finder's scratch, then the suppression bitmap (also the sorted form's bitmap)
+  const int sw = iter_scratch_words(NT, NR, SH);
   uint32_t* cm = sm;
-  uint32_t* gone = sm + NT;
+  uint32_t* gone = sm + (sw > cap ? sw : cap);
   const int nwords = (NT * NR + 31) >> 5;
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) gone[i] = 0u;
   __syncthreads();
   GlobalCells cells{acc + e * (long long)NT * NR, gone, NR};
-  const int n = extract_iterative(cells, NT, NR, thr, rel_num, rel_den, R, maxp, cm, peaks + e * maxp, s_sel);
+  const int n =
+      extract_iterative(cells, NT, NR, SH, thr, rel_num, rel_den, R, maxp, cm, cap, gone, peaks + e * maxp, s_sel);
   if (threadIdx.x == 0) {
     npeaks[e] = n;
     if (n > maxp) atomicOr(status, HOUGH_F_PEAK_OVERFLOW);
@@ -364,13 +368,21 @@ cudaError_t launch_peaks(const int16_t* acc, long long n_events, const hough_par
                          hough_peak* peaks, int* status, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;
   if (p.peak_mode == HOUGH_PEAK_ITERATIVE) {
-    const int smem = (p.n_theta + (p.n_theta * p.n_rho + 31) / 32) * 4;
+    // slices of 32 rows, or taller ones where the maxima and the suppression bitmap would not
+    // fit in shared memory; then as many candidate keys for the sorted form as the rest holds
+    const int nwords = (p.n_theta * p.n_rho + 31) / 32, budget = 200 * 1024 / 4;
+    int SH = 32;
+    while (iter_scratch_words(p.n_theta, p.n_rho, SH) + nwords > budget) SH *= 2;
+    const int sw = iter_scratch_words(p.n_theta, p.n_rho, SH);
+    int cap = 16384;
+    while (cap > 0 && (cap > sw ? cap : sw) + nwords > budget) cap = cap > 1024 ? cap / 2 : 0;
+    const int smem = ((cap > sw ? cap : sw) + nwords) * 4;
     cudaError_t err = cudaFuncSetAttribute((const void*)peaks_iterative_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    peaks_iterative_kernel<<<(unsigned)n_events, 512, smem, st>>>(acc, p.n_theta, p.n_rho, p.threshold, p.rel_num,
-                                                                  p.rel_den, p.nms_radius, p.max_peaks, npeaks,
-                                                                  peaks, status);
+    peaks_iterative_kernel<<<(unsigned)n_events, 512, smem, st>>>(acc, p.n_theta, p.n_rho, SH, cap, p.threshold,
+                                                                  p.rel_num, p.rel_den, p.nms_radius, p.max_peaks,
+                                                                  npeaks, peaks, status);
     return cudaGetLastError();
   }
   peaks_kernel<<<(unsigned)n_events, 256, 0, st>>>(acc, p.n_theta, p.n_rho, p.threshold, p.max_peaks, npeaks, peaks,

@@ -420,6 +420,10 @@ ITER = [  # (workload, events, n_theta, n_rho, threshold, rel_num, rel_den, nms_
     ("plain_small", 30, 64, 64, 6, 0, 1, 0, 300),    # no relative cut, no neighbourhood: every cell >= T
     ("plain_paper", 30, 100, 63, 8, 1, 4, 2, 512),   # N_theta not a multiple of 64, odd N_rho
     ("plain_paper", 20, 256, 256, 16, 1, 10, 1, 8),  # overflow: more peaks than stored
+    # 20k-40k candidates an event, above the sorted form's 8,192 keys: one pass per peak
+    ("batched", 12, 256, 256, 4, 0, 1, 6, 512),
+    # 1k-10k candidates: events of both forms in one launch, sorts of up to 8,192 keys
+    ("batched", 40, 256, 256, 16, 1, 3, 3, 1024),
 ]
 
 
@@ -441,6 +445,30 @@ def test_iterative_fused_and_stepwise_match_oracle(h, name, n, nt, nr, thr, num,
     npk, pk = h.peaks(acc, p, st)
     assert np.array_equal(to_np(npk), ref.npeaks)
     assert np.array_equal(peaks_np(pk), peaks_np(torch.from_numpy(ref.peaks.view(np.int16).reshape(n, mx, 4))))
+
+
+def test_iterative_cell_above_4095_votes(h):
+    """4,200 copies of one hit put 4,200 votes into a cell of every column: beyond the 12-bit vote
+    field of the sorted form's keys, so that event takes one pass per peak; its neighbours in the
+    batch take the sorted form. Fused, batched and stepwise results as the oracle's."""
+    ev = gen.generate(gen.CONFIGS["plain_paper"], 3)
+    a, b = int(ev.off[1]), int(ev.off[2])
+    xy = np.concatenate([ev.xy[:b], np.repeat(ev.xy[a:a + 1], 4200, axis=0), ev.xy[b:]])
+    off = ev.off.copy()
+    off[2:] += 4200
+    n_t, n_r = 128, 128
+    op = oracle.params(n_t, n_r, 10, 1, 512, peak_mode=1, rel_num=1, rel_den=2, nms_radius=2)
+    ref = oracle.run(xy, off, op, with_acc=True, threads=THREADS)
+    assert ref.acc.reshape(3, n_t, n_r)[1].max() >= 4200
+    p = h.params(n_t, n_r, 10, 1, 512, peak_mode=1, rel_num=1, rel_den=2, nms_radius=2)
+    d_xy, d_off = torch.from_numpy(xy).cuda(), torch.from_numpy(off).cuda()
+    for batched in (False, True):
+        out = h.run(d_xy, d_off, p, checksum=True, batched=batched)
+        assert h.status(out.status) == ref.status
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, off, checksum=out.checksum)
+    npk, pk = h.peaks(torch.from_numpy(ref.acc).cuda(), p, h.new_status())
+    assert np.array_equal(to_np(npk), ref.npeaks)
+    assert np.array_equal(peaks_np(pk), peaks_np(torch.from_numpy(ref.peaks.view(np.int16).reshape(3, 512, 4))))
 
 
 def test_iterative_stepwise_large_accumulator(h):
