@@ -91,14 +91,15 @@ static bool layout(Plan& pl) {
   {
     int iter_words = 0;
     if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
-      const int sorted_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 31) / 32;
+      // candidate keys, then 2 state bits a cell (also room for the walk's 1-bit bitmap)
+      const int cand_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 15) / 16;
       iter_words = iter_scratch_words(pl.n_theta, pl.n_rho, kIterSliceRows);
-      if (pl.iter_cap > 0 && sorted_words > iter_words) iter_words = sorted_words;
+      if (pl.iter_cap > 0 && cand_words > iter_words) iter_words = cand_words;
     }
     o += round16((wpad * pl.nrb > iter_words ? wpad * pl.nrb : iter_words) * 4);
   }
-  pl.off_cnt = o;
-  o += round16(wpad * pl.key_groups * 4);
+  pl.off_cnt = o;  // peak-record keys of the local-maximum scan (the iterative finder has none)
+  if (pl.peak_mode != HOUGH_PEAK_ITERATIVE) o += round16(wpad * pl.key_groups * 4);
   pl.off_unres = o;
   o += round16((pl.hit_cap + 1024) / 32 * 4);
   pl.off_trig = o;

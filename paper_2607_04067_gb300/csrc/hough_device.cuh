@@ -272,24 +272,46 @@ __device__ __forceinline__ void or_bits(uint32_t* bm, int b0, int b1) {
   }
 }
 
-// The iterative finder (Sec. 2) in sorted form. Taking the unsuppressed cell with the most votes
-// (raster order on ties) and suppressing its window, until the best cell fails the threshold, is
-// the same as walking the cells that pass the threshold in that order and keeping each one that
-// no window kept so far covers: every cell ranked above the next peak is a peak or lies in a
-// kept window, so the first uncovered candidate is the cell the one-pass-per-peak form takes.
-// Candidates are cells with votes >= max(thr, ceil(rel_num * amax / rel_den)), keyed
-// (votes << 20) | ((1023 - j) << 10) | (1023 - k), so that the larger key comes first.
-// keys: cap words, sup: a zeroed bitmap of n_theta * n_rho bits (cell (j, k) is bit j NR + k),
-// both shared. The CTA finds the maximum, collects and sorts the keys (bitonic); warp 0 walks
-// them 32 at a time: lanes drop candidates covered by earlier chunks' windows, then the lowest
-// remaining lane is kept and the lanes its window covers drop out, until none remain; the
-// kept windows go into the bitmap for the next chunks.
-// Returns the true count, or -1 (written nothing) when the maximum exceeds 4095 votes or the
-// candidates exceed cap: those take the per-pass form. s: 2 ints of shared scratch.
+// Sorts n (a power of two) shared keys into descending order (bitonic); all threads call it.
+__device__ __forceinline__ void bitonic_desc(uint32_t* keys, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+        const int i = 2 * t - (t & (stride - 1)), l = i + stride;
+        const uint32_t a = keys[i], b = keys[l];
+        if (((i & size) == 0) == (a < b)) {
+          keys[i] = b;
+          keys[l] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ void store_peak(hough_peak* dst, uint32_t key) {
+  hough_peak pk;
+  pk.theta_bin = (int16_t)(1023 - (int)((key >> 10) & 1023u));
+  pk.rho_bin = (int16_t)(1023 - (int)(key & 1023u));
+  pk.votes = (int16_t)(key >> 20);
+  pk.flags = 0;
+  *dst = pk;
+}
+
+// The iterative finder (Sec. 2) in candidate form. Taking the unsuppressed cell with the most
+// votes (raster order on ties) and suppressing its window, until the best cell fails the
+// threshold, keeps exactly the candidates (cells with votes >= max(thr, ceil(rel_num amax /
+// rel_den))) that no kept candidate ranked above them covers, in rank order: every cell ranked
+// above the next peak is a peak or lies in a kept window. Candidates are keyed
+// (votes << 20) | ((1023 - j) << 10) | (1023 - k), the larger key ranking first. The window
+// relation is symmetric, so a candidate's dominators (higher-ranked candidates whose window
+// covers it) are the higher-ranked candidates in its own window.
+// Stage 1 (all threads): the maximum, then the candidate keys in any order (keys: cap words).
+// Returns C, or -1 when the maximum exceeds 4095 votes or C exceeds cap. s[0], s[1] used.
 template <class Cells>
-__device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, int rel_num, int rel_den, int R,
-                                        int maxp, uint32_t* keys, int cap, uint32_t* sup, hough_peak* dst, int* s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, bd = blockDim.x;
+__device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel_num, int rel_den, uint32_t* keys,
+                                  int cap, int* s, int* tq_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     s[0] = 0;
     s[1] = 0;
@@ -308,7 +330,7 @@ __device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, i
   if (amax > 4095) return -1;  // uniform: every thread read the same value
   const long long need = ((long long)rel_num * amax + rel_den - 1) / rel_den;
   const int tq = (int)max((long long)thr, need);
-  // the candidates, in any order; the count may exceed cap (then only counted)
+  *tq_out = tq;
   for (int k = warp; k < NR; k += nwarps) {
     for (int j0 = 0; j0 < NT; j0 += 32) {
       const int j = j0 + lane;
@@ -326,27 +348,134 @@ __device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, i
   }
   __syncthreads();
   const int C = s[1];
-  if (C > cap) return -1;
+  return C > cap ? -1 : C;
+}
+
+// Stage 2, in parallel rounds (all threads): st holds 2 bits per cell (cell (j, k) is pair
+// j NR + k): 0 not a candidate, 1 undecided, 2 dropped, 3 kept; a candidate's owner thread
+// changes them with one atomic, so readers see a whole state. Each round, an undecided
+// candidate with a kept cell in its window is dropped (a kept cell in the window of an
+// undecided one always ranks above it: otherwise that one would have been dropped before the
+// cell was kept), and one with no undecided higher-ranked cell in its window is kept. Decisions
+// are final, and each round decides at least the highest-ranked undecided candidate; states
+// read while others change are either the old or the final one, which only speeds this up.
+// The kept keys are then gathered into st (as many as its st_words hold) and sorted. Returns
+// the count, or -1 (written nothing) past 64 rounds or st_words, or with more than 64
+// candidates a thread. s[2] .. s[5] used.
+template <class Cells>
+__device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int maxp, const uint32_t* keys, int C,
+                              uint32_t* st, int st_words, hough_peak* dst, int* s) {
+  const int lane = threadIdx.x & 31, bd = blockDim.x;
+  if (C > 64 * bd) return -1;
+  const int nst = (NT * NR + 15) >> 4;
+  for (int i = threadIdx.x; i < nst; i += bd) st[i] = 0u;
+  if (threadIdx.x < 4) s[2 + threadIdx.x] = 0;
+  __syncthreads();
+  auto cell_of = [&](uint32_t key) { return (1023 - (int)((key >> 10) & 1023u)) * NR + 1023 - (int)(key & 1023u); };
+  for (int i = threadIdx.x; i < C; i += bd) {
+    const int c = cell_of(keys[i]);
+    atomicOr(&st[c >> 4], 1u << ((c & 15) << 1));
+  }
+  __syncthreads();
+  for (int round = 0;; ++round) {
+    if (round == 64) return -1;  // uniform
+    int und = 0;
+    for (int i = threadIdx.x; i < C; i += bd) {
+      const uint32_t key = keys[i];
+      const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+      const int c = j * NR + k;
+      if (((st[c >> 4] >> ((c & 15) << 1)) & 3u) != 1u) continue;
+      bool drop = false, all = true;
+      const int k0 = max(0, k - R), k1 = min(NR - 1, k + R);
+      for (int a = -R; a <= R && !drop; ++a) {
+        int jj = j + a, r0 = k0, r1 = k1;
+        if (jj < 0 || jj >= NT) {
+          jj = jj < 0 ? jj + NT : jj - NT;
+          r0 = NR - 1 - k1;
+          r1 = NR - 1 - k0;
+        }
+        // the states of rows r0 .. r1 of column jj, 16 cells at a time
+        const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
+        for (int off = 0; off < nb && !drop; off += 32) {
+          const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
+          uint32_t f = st[w] >> sh;
+          if (sh && sh + len > 32) f |= st[w + 1] << (32 - sh);
+          if (len < 32) f &= (1u << len) - 1u;
+          if ((f & (f >> 1)) & 0x55555555u) {  // a kept cell
+            drop = true;
+            break;
+          }
+          uint32_t m = f & ~(f >> 1) & 0x55555555u;  // undecided cells
+          while (m && all) {
+            const int t = __ffs(m) - 1;
+            const int kr = r0 + ((off + t) >> 1);
+            const uint32_t kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) |
+                                (uint32_t)(1023 - kr);
+            if (kd > key) all = false;  // an undecided cell ranked above (the cell itself is equal)
+            m &= m - 1u;
+          }
+        }
+      }
+      if (drop) atomicXor(&st[c >> 4], 3u << ((c & 15) << 1));  // 1 -> 2
+      else if (all) atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+      else ++und;
+    }
+    // undecided count: three rotating counters, so that one barrier a round suffices
+    const int r3 = round % 3;
+    und = __reduce_add_sync(0xffffffffu, und);
+    if (lane == 0 && und) atomicAdd(&s[2 + r3], und);
+    if (threadIdx.x == 0) s[2 + (r3 + 1) % 3] = 0;
+    __syncthreads();
+    if (s[2 + r3] == 0) break;
+  }
+  // the kept keys, gathered into st once every state has been read
+  unsigned long long flags = 0;
+  {
+    int t = 0;
+    for (int i = threadIdx.x; i < C; i += bd, ++t) {
+      const int c = cell_of(keys[i]);
+      if (((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 3u) flags |= 1ull << t;
+    }
+  }
+  {
+    const int kept = __reduce_add_sync(0xffffffffu, __popcll(flags));
+    if (lane == 0 && kept) atomicAdd(&s[5], kept);
+  }
+  __syncthreads();
+  const int nk = s[5];
+  int N = 32;
+  while (N < nk) N <<= 1;
+  if (N > st_words) return -1;  // uniform; st is not needed by the other forms
+  if (threadIdx.x == 0) s[4] = 0;
+  __syncthreads();
+  {
+    int t = 0;
+    for (int i = threadIdx.x; i < C; i += bd, ++t) {
+      if ((flags >> t) & 1ull) st[atomicAdd(&s[4], 1)] = keys[i];
+    }
+  }
+  for (int i = nk + threadIdx.x; i < N; i += bd) st[i] = 0u;
+  __syncthreads();
+  bitonic_desc(st, N);
+  for (int i = threadIdx.x; i < min(nk, maxp); i += bd) store_peak(dst + i, st[i]);
+  __syncthreads();
+  return nk;
+}
+
+// Stage 2, as one walk (sup: a shared bitmap of NT NR bits, cell (j, k) bit j NR + k): the CTA
+// sorts the keys (cap words, past C free), then warp 0 walks them 32 at a time: lanes drop
+// candidates covered by earlier chunks' windows, then the lowest remaining lane is kept and the
+// lanes its window covers drop out, until none remain; the kept windows go into the bitmap for
+// the next chunks. Returns the count. s[0] used.
+__device__ inline int resolve_walk(int NT, int NR, int R, int maxp, uint32_t* keys, int C, uint32_t* sup,
+                                   hough_peak* dst, int* s) {
+  const int lane = threadIdx.x & 31, bd = blockDim.x;
   int N = 32;
   while (N < C) N <<= 1;
   for (int i = C + threadIdx.x; i < N; i += bd) keys[i] = 0u;
-  const int nbits = NT * NR;
-  for (int i = threadIdx.x; i < (nbits + 31) >> 5; i += bd) sup[i] = 0u;
+  for (int i = threadIdx.x; i < (NT * NR + 31) >> 5; i += bd) sup[i] = 0u;
   __syncthreads();
-  // bitonic sort, descending
-  for (int size = 2; size <= N; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < (N >> 1); t += bd) {
-        const int i = 2 * t - (t & (stride - 1)), l = i + stride;
-        const uint32_t a = keys[i], b = keys[l];
-        if (((i & size) == 0) == (a < b)) {
-          keys[i] = b;
-          keys[l] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
+  bitonic_desc(keys, N);
   if (threadIdx.x < 32) {
     const int W = 2 * R + 1;
     const uint32_t mW = ((1u << 21) + W - 1) / W;  // item / W = (item * mW) >> 21, exact here
@@ -354,7 +483,7 @@ __device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, i
     for (int base = 0; base < C; base += 32) {
       const int idx = base + lane;
       const uint32_t key = keys[idx];  // idx < N: zero past C
-      const int v = (int)(key >> 20), j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+      const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int cb = j * NR + k;
       const bool live = idx < C && !((sup[cb >> 5] >> (cb & 31)) & 1u);
       uint32_t L = __ballot_sync(0xffffffffu, live), A = 0;
@@ -369,14 +498,7 @@ __device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, i
       if (na) {
         const bool kept = (A >> lane) & 1u;
         const int r = __popc(A & ((1u << lane) - 1u));
-        if (kept && n + r < maxp) {
-          hough_peak pk;
-          pk.theta_bin = (int16_t)j;
-          pk.rho_bin = (int16_t)k;
-          pk.votes = (int16_t)v;
-          pk.flags = 0;
-          dst[n + r] = pk;
-        }
+        if (kept && n + r < maxp) store_peak(dst + n + r, key);
         // this chunk's keys are in registers now: its words hold the kept cells
         __syncwarp();
         if (kept) keys[base + r] = (uint32_t)jk;
@@ -406,18 +528,26 @@ __device__ int extract_iterative_sorted(Cells& cells, int NT, int NR, int thr, i
   return n;
 }
 
-// The iterative finder: the sorted form where it applies (cap > 0), else one pass per peak.
-// scratch: shared words for both forms, which never run at the same time:
-// max(iter_scratch_words(NT, NR, SH), cap + ceil(NT NR / 32)) when sup is null (the sorted
-// form's bitmap then follows its cap keys), else max(iter_scratch_words(NT, NR, SH), cap) with
-// sup a shared bitmap of NT NR bits that the sorted form may use (and leaves set).
+// The iterative finder: the candidate form where it applies (cap > 0): resolved in rounds when
+// st_words > 0, else (or when the rounds give up) by the walk; otherwise one pass per peak.
+// scratch (shared): max(iter_scratch_words(NT, NR, SH), cap + max(ceil(NT NR / 32), st_words))
+// words when sup is null: the candidate keys, then the walk's bitmap, or the rounds' states
+// (st_words >= ceil(NT NR / 16), a power of two). With sup given (a shared bitmap of NT NR
+// bits, left set) the walk uses it, and scratch needs max(iter_scratch_words, cap + st_words).
 template <class Cells>
 __device__ int extract_iterative(Cells& cells, int NT, int NR, int SH, int thr, int rel_num, int rel_den, int R,
-                                 int maxp, uint32_t* scratch, int cap, uint32_t* sup, hough_peak* dst, int* s) {
+                                 int maxp, uint32_t* scratch, int cap, uint32_t* sup, int st_words,
+                                 hough_peak* dst, int* s) {
   if (cap > 0) {
-    const int n = extract_iterative_sorted(cells, NT, NR, thr, rel_num, rel_den, R, maxp, scratch, cap,
-                                           sup ? sup : scratch + cap, dst, s);
-    if (n >= 0) return n;
+    int tq = 0;
+    const int C = collect_candidates(cells, NT, NR, thr, rel_num, rel_den, scratch, cap, s, &tq);
+    if (C >= 0) {
+      if (st_words > 0) {
+        const int n = resolve_rounds(cells, NT, NR, R, tq, maxp, scratch, C, scratch + cap, st_words, dst, s);
+        if (n >= 0) return n;
+      }
+      return resolve_walk(NT, NR, R, maxp, scratch, C, sup ? sup : scratch + cap, dst, s);
+    }
   }
   return extract_iterative_passes(cells, NT, NR, SH, thr, rel_num, rel_den, R, maxp, scratch, dst, s);
 }

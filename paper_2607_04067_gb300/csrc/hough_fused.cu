@@ -1311,7 +1311,8 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       }
       __syncthreads();
       return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
-                               maxp, pbits, pl.iter_cap, nullptr, io.peaks + e * (long long)maxp, sh.tmp);
+                               maxp, pbits, pl.iter_cap, nullptr, (NT * NR + 15) >> 4,
+                               io.peaks + e * (long long)maxp, sh.tmp);
     };
     total = pl.mp ? iterative(FusedCells<A32, true>{acc, Wd, nrp, pl.rows_phys})
                   : iterative(FusedCells<A32, false>{acc, Wd, nrp, pl.rows_phys});

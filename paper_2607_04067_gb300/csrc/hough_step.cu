@@ -314,7 +314,7 @@ __global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, 
                                        int rel_num, int rel_den, int R, int maxp, int* npeaks, hough_peak* peaks,
                                        int* status) {
   extern __shared__ uint32_t sm[];
-  __shared__ int s_sel[2];
+  __shared__ int s_sel[8];
   const long long e = blockIdx.x;
   // the finder's scratch, then the suppression bitmap (also the sorted form's bitmap)
   const int sw = iter_scratch_words(NT, NR, SH);
@@ -325,7 +325,7 @@ __global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, 
   __syncthreads();
   GlobalCells cells{acc + e * (long long)NT * NR, gone, NR};
   const int n =
-      extract_iterative(cells, NT, NR, SH, thr, rel_num, rel_den, R, maxp, cm, cap, gone, peaks + e * maxp, s_sel);
+      extract_iterative(cells, NT, NR, SH, thr, rel_num, rel_den, R, maxp, cm, cap, gone, 0, peaks + e * maxp, s_sel);
   if (threadIdx.x == 0) {
     npeaks[e] = n;
     if (n > maxp) atomicOr(status, HOUGH_F_PEAK_OVERFLOW);
