@@ -264,6 +264,65 @@ def track_finding(h, cfg, out, p, first_event: int, n_sample: int, dpt_max=20.0,
             "dphi_rms_mrad": float(1e3 * np.sqrt(np.mean(np.square(dphi)))) if dphi else None}
 
 
+def run_phase_split(args, cfg):
+    """Cycles per event of each phase of the fused kernel against CTA size (the paper's
+    per-stage study, Sec. 4). The phase-timer build of the library (HOUGH_PHASE_TIMERS, same
+    results) runs the batched launch of the workload's first events once per block size after
+    warm-up; thread 0 of every CTA adds the clock64() cycles of each phase of its items. One
+    JSON line: per block size, cycles per event by phase (summed over the CTAs, divided by
+    the events) and the events/s of that instrumented launch."""
+    os.environ["HOUGH_PHASE_TIMERS"] = "1"
+    import torch
+    import paper_2607_04067_gb300 as h
+
+    torch.cuda.set_device(0)
+    n = args.events or min(cfg.n_events, 20000)
+    ev = gen.generate(cfg, n, with_truth=False)
+    xy, off = torch.from_numpy(ev.xy).cuda(), torch.from_numpy(ev.off).cuda()
+    stream = torch.cuda.Stream()
+    rows, peak = {}, peak_args(args)
+    for blk in (int(x) for x in args.phase_split.split(",")):
+        p = None
+        for tiles in (1, 0):  # one tile where the accumulator fits one CTA
+            q = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks, theta_tiles=tiles,
+                         block=blk, events_per_cta=1)
+            q.peak_mode, q.rel_num, q.rel_den, q.nms_radius = peak
+            try:
+                h.resolve(q)
+                p = q
+                break
+            except h.HoughError:
+                continue
+        if p is None:
+            rows[str(blk)] = {"unavailable": "no plan with this block size"}
+            continue
+        out = h.alloc_outputs(ev.n_hits, n, p)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                h.run(xy, off, p, out=out, batched=True, stream=stream)
+        stream.synchronize()
+        h.phase_cycles(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            h.run(xy, off, p, out=out, batched=True, stream=stream)
+            e1.record(stream)
+        e1.synchronize()
+        enabled, cyc = h.phase_cycles(reset=True)
+        if not enabled:
+            raise RuntimeError("the library loaded is not the phase-timer build")
+        if h.status(out.status, stream) != 0:
+            raise RuntimeError("device status flags set")
+        r = h.resolve(p)
+        rows[str(blk)] = {"theta_tiles": r.theta_tiles, "events_per_s": n / (e0.elapsed_time(e1) * 1e-3),
+                          "cycles_per_event": {k: round(v / n) for k, v in cyc.items() if v}}
+    print(json.dumps({"metric": "fused-kernel cycles per event by phase (thread 0 of each CTA)",
+                      "workload": cfg.name, "events": n, "hits": ev.n_hits, "n_theta": cfg.n_theta,
+                      "n_rho": cfg.n_rho, "peak_finder": args.peak_mode, "build": "phase timers",
+                      "rows": rows}))
+    return 0
+
+
 def run_sweep(args, cfg):
     """Batch-size sweep on one GPU (the paper's runtime-versus-event-count study, Sec. 4): for
     each batch of the workload's first n events, events/s of the batched launch (persistent
@@ -364,12 +423,16 @@ def main():
     ap.add_argument("--sweep", default="", help="batch-size sweep instead of the benchmark, e.g. '1,10,100,1000'")
     ap.add_argument("--sweep-stepwise-max", type=int, default=10000, help="largest batch run through the stepwise path")
     ap.add_argument("--sweep-oracle-max", type=int, default=10000, help="largest batch timed on the CPU oracle")
+    ap.add_argument("--phase-split", default="",
+                    help="per-phase cycles of the fused kernel for these block sizes, e.g. '256,512,1024'")
     args = ap.parse_args()
     cfg = gen.CONFIGS[args.workload]
     if args.impl == "reference":
         return run_reference(args, cfg)
     if args.sweep:
         return run_sweep(args, cfg)
+    if args.phase_split:
+        return run_phase_split(args, cfg)
 
     import torch
     import paper_2607_04067_gb300 as h

@@ -333,6 +333,35 @@ int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t 
 int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,
                              unsigned long long* d_sink, void* stream);
 
+/* Phases of a fused-kernel item, in order, for hough_phase_cycles. The iterative finder's
+ * phases replace the scan's; SCAN is then the accumulator checksum before the finder. */
+#define HOUGH_PHASE_CLEAR 0         /* zero the accumulator, halo and peak bitmap */
+#define HOUGH_PHASE_STAGE 1         /* map hits into shared memory (all chunks) */
+#define HOUGH_PHASE_VOTE 2          /* votes (all chunks) */
+#define HOUGH_PHASE_FOLD 3          /* guard rows of the mirror-pair layout */
+#define HOUGH_PHASE_SCAN 4          /* 3x3 local-maximum scan (or the checksum, iterative finder) */
+#define HOUGH_PHASE_EXSCAN 5        /* block scan of the peak-record keys */
+#define HOUGH_PHASE_RECORDS 6       /* peak records */
+#define HOUGH_PHASE_MERGE 7         /* theta tiles: publish and merge */
+#define HOUGH_PHASE_IT_MAX 8        /* iterative finder: accumulator maximum */
+#define HOUGH_PHASE_IT_COLLECT 9    /* iterative finder: candidates */
+#define HOUGH_PHASE_IT_RESOLVE 10   /* iterative finder: kept set (rounds, walk or passes) */
+#define HOUGH_PHASE_IT_ORDER 11     /* iterative finder: kept keys sorted, records */
+#define HOUGH_PHASE_SEL_COLUMNS 12  /* selection: peak columns and their trig values */
+#define HOUGH_PHASE_SEL_BITMAPS 13  /* selection: dilated peak bitmaps */
+#define HOUGH_PHASE_SEL_A 14        /* selection: a lane per hit over the first peak columns */
+#define HOUGH_PHASE_SEL_B 15        /* selection: the rest, and the event outputs */
+#define HOUGH_PHASE_COUNT 16
+
+/* Per-phase cycle counters of the fused kernel, in a library built with HOUGH_PHASE_TIMERS
+ * defined (`_build.build(variant="phase")`): thread 0 of every CTA adds the clock64() cycles
+ * since its previous mark to the counter of the phase that just ended, so a counter over a
+ * launch divided by its events is the cycles an event spends in that phase on one SM.
+ * Synchronises the device, copies min(n, HOUGH_PHASE_COUNT) counters to host_cycles and,
+ * with reset != 0, zeroes them. *enabled (may be null) is 1 in the timer build and 0
+ * otherwise (the counters then read 0). HOUGH_EINVAL for a null host_cycles or n < 0. */
+int hough_phase_cycles(uint64_t* host_cycles, int32_t n, int32_t reset, int32_t* enabled);
+
 #ifdef __cplusplus
 }
 #endif

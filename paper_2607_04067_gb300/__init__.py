@@ -57,6 +57,9 @@ class ServeResult(ctypes.Structure):
 
 
 PEAK_LOCAL_MAX, PEAK_ITERATIVE = 0, 1
+# HOUGH_PHASE_* of include/hough.h, in order
+PHASES = ("clear", "stage", "vote", "fold", "scan", "exscan", "records", "merge", "it_max", "it_collect",
+          "it_resolve", "it_order", "sel_columns", "sel_bitmaps", "sel_a", "sel_b")
 
 
 def params(n_theta: int, n_rho: int, threshold: int, keep_halfwidth: int = 1, max_peaks: int = 1024,
@@ -80,7 +83,9 @@ def load(build: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build else _build.LIB
+            # HOUGH_PHASE_TIMERS=1 selects the phase-timer build (same results, per-phase cycles)
+            variant = "phase" if os.environ.get("HOUGH_PHASE_TIMERS") == "1" else None
+            path = _build.build(variant=variant) if build else _build.lib_path(variant)
             lib = ctypes.CDLL(path)
             vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
             P = ctypes.POINTER(Params)
@@ -101,6 +106,7 @@ def load(build: bool = True):
                 "hough_run_batched_static": [vp, i64, vp, i64, P, vp, vp, vp, vp, vp, vp, vp],
                 "hough_autotune": [P, vp, i64, vp, i64, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(ctypes.c_float)],
                 "hough_circles": [vp, vp, i64, P, ctypes.c_double, vp, vp],
+                "hough_phase_cycles": [vp, i32, i32, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -486,6 +492,17 @@ def selftest_fpbin(n_theta: int, n_rho: int, seed: int, n_samples: int, stream=N
     _check("hough_selftest_fpbin", load().hough_selftest_fpbin(n_theta, n_rho, seed, n_samples, _ptr(out),
                                                                _stream(stream)))
     return tuple(int(x) for x in out.tolist())
+
+
+def phase_cycles(reset: bool = True):
+    """(enabled, {phase: cycles}) of the fused kernel's phase counters since the last reset
+    (thread 0 of every CTA, summed). enabled is False unless the library is the phase-timer
+    build (HOUGH_PHASE_TIMERS=1 in the environment before the first load); the counts are
+    then 0. Synchronises the device."""
+    buf = (ctypes.c_uint64 * len(PHASES))()
+    en = ctypes.c_int32(0)
+    _check("hough_phase_cycles", load().hough_phase_cycles(buf, len(PHASES), 1 if reset else 0, ctypes.byref(en)))
+    return bool(en.value), {name: int(buf[i]) for i, name in enumerate(PHASES)}
 
 
 def probe_smem_atomics(mode: int, ctas_per_sm: int, threads: int, smem_bytes: int, iters: int, sink, stream=None):

@@ -15,6 +15,37 @@
 
 namespace hgpu {
 
+// Phase timers (builds with HOUGH_PHASE_TIMERS defined): thread 0 of a CTA adds the clock64()
+// cycles since its previous mark to the counter of the phase that just ended (HOUGH_PHASE_*).
+// The mark lives in shared memory; the counters are per translation unit, and the fused
+// kernel's are the ones hough_phase_cycles reads. Without the define the marks compile away.
+#ifdef HOUGH_PHASE_TIMERS
+static __device__ unsigned long long g_phase_cycles[HOUGH_PHASE_COUNT];
+__device__ __forceinline__ unsigned long long& phase_mark() {
+  __shared__ unsigned long long t;
+  return t;
+}
+#define HOUGH_PHASE_START()                                     \
+  do {                                                          \
+    if (threadIdx.x == 0) hgpu::phase_mark() = clock64();       \
+  } while (0)
+#define HOUGH_PHASE(p)                                                          \
+  do {                                                                          \
+    if (threadIdx.x == 0) {                                                     \
+      const unsigned long long t_ = clock64();                                  \
+      atomicAdd(&hgpu::g_phase_cycles[(p)], t_ - hgpu::phase_mark());           \
+      hgpu::phase_mark() = t_;                                                  \
+    }                                                                           \
+  } while (0)
+#else
+#define HOUGH_PHASE_START() \
+  do {                      \
+  } while (0)
+#define HOUGH_PHASE(p) \
+  do {                 \
+  } while (0)
+#endif
+
 constexpr long long kH = HOUGH_RHO_HALF_RANGE;
 constexpr int kTwoHm1 = (int)(2 * kH - 1);  // 1407374883 < 2^31
 // |u_q|, |v_q| <= kFast32 keeps u c + v s + H inside int32: 2 * 44061 * 2^14 + H < 2^31.
@@ -246,6 +277,7 @@ __device__ int extract_iterative_passes(Cells& cells, int NT, int NR, int SH, in
     if (lane == 0) s[0] = n;
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_RESOLVE);
   const int n = s[0];
   __syncthreads();
   return n;
@@ -326,6 +358,7 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
     if (lane == 0 && m) atomicMax(&s[0], m);
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_MAX);
   const int amax = s[0];
   if (amax > 4095) return -1;  // uniform: every thread read the same value
   const long long need = ((long long)rel_num * amax + rel_den - 1) / rel_den;
@@ -347,6 +380,7 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
     }
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_COLLECT);
   const int C = s[1];
   return C > cap ? -1 : C;
 }
@@ -428,6 +462,7 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     __syncthreads();
     if (s[2 + r3] == 0) break;
   }
+  HOUGH_PHASE(HOUGH_PHASE_IT_RESOLVE);
   // the kept keys, gathered into st once every state has been read
   unsigned long long flags = 0;
   {
@@ -459,6 +494,7 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
   bitonic_desc(st, N);
   for (int i = threadIdx.x; i < min(nk, maxp); i += bd) store_peak(dst + i, st[i]);
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_ORDER);
   return nk;
 }
 
@@ -523,6 +559,7 @@ __device__ inline int resolve_walk(int NT, int NR, int R, int maxp, uint32_t* ke
     if (lane == 0) s[0] = n;
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_RESOLVE);
   const int n = s[0];
   __syncthreads();
   return n;

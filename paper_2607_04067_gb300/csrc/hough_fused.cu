@@ -966,6 +966,7 @@ __device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx
     if (lane == 0) unres[(i0 >> 5) + warp] = hbits;
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_SEL_A);
   if (D > cap) {
     // Open hits come in runs (staging order follows the input), so warp w takes hit
     // 32 j + w of every word j, sweeping 32 words per ballot: runs spread over all warps.
@@ -1072,6 +1073,7 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
     }
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_SEL_COLUMNS);
   const int D = sh.D;
   const int hw = pl.keep_hw;
   if (from_bits) {
@@ -1114,6 +1116,7 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   }
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_SEL_BITMAPS);
   int kept = 0;
   if (D == 0) {
     for (int i = tid; i < n; i += bd) io.mask[a + i] = 0;
@@ -1237,6 +1240,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
 
   // 1. clear accumulator, halo columns, peak bitmap and counters
   __syncthreads();
+  HOUGH_PHASE_START();
   {
     uint4* z = reinterpret_cast<uint4*>(smem + pl.off_acc);
     const int nz = pl.region_bytes >> 4;
@@ -1252,6 +1256,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   for (int h0 = 0; h0 < n; h0 += pl.hit_cap) {
     const int cn = min(pl.hit_cap, n - h0);
     __syncthreads();
+    HOUGH_PHASE(h0 == 0 ? HOUGH_PHASE_CLEAR : HOUGH_PHASE_VOTE);
     if (tid == 0) {
       sh.nv = 0;
       sh.wide = 0;
@@ -1260,6 +1265,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     stage_vote32(io.xy, a + h0, cn, hb, &sh.nv, &sh.wide, pl.fpbin != 0, pl.mp ? pl.mp_lsq : 0,
                  pl.mp ? reinterpret_cast<uint16_t*>(smem + pl.off_idx) : nullptr);
     __syncthreads();
+    HOUGH_PHASE(HOUGH_PHASE_STAGE);
     if (tid == 0) {
       if (sh.wide & 2) sh.flags |= HOUGH_F_BAD_HIT;
       if (sh.wide & 1) sh.reuse = 0;  // wide hits are not in the staged list
@@ -1288,6 +1294,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     }
   }
   __syncthreads();
+  HOUGH_PHASE(n > 0 ? HOUGH_PHASE_VOTE : HOUGH_PHASE_CLEAR);
 
   // 3-4. peaks
   const int maxp = pl.max_peaks;
@@ -1299,6 +1306,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     if (pl.mp) {
       mp_fold(pl, acc, Wd, nullptr);
       __syncthreads();
+      HOUGH_PHASE(HOUGH_PHASE_FOLD);
     }
     auto iterative = [&](auto cells) {
       if (do_cs) {
@@ -1310,6 +1318,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
         cs_tile = block_sum_u64(cs, sh.red);
       }
       __syncthreads();
+      HOUGH_PHASE(HOUGH_PHASE_SCAN);
       return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
                                maxp, pbits, pl.iter_cap, nullptr, (NT * NR + 15) >> 4,
                                io.peaks + e * (long long)maxp, sh.tmp);
@@ -1324,6 +1333,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     if (pl.mp) {
       mp_fold(pl, acc, Wd, T > 1 ? halo : nullptr);
       __syncthreads();
+      HOUGH_PHASE(HOUGH_PHASE_FOLD);
       scan_mp(pl, acc, halo, aw, Wd, pbits, do_cs, csum);
     } else if (packed) {
       scan_packed(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
@@ -1331,6 +1341,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       scan_scalar<A32>(pl, acc, halo, pbits, wt, T, j0, do_cs, csum);
     }
     __syncthreads();
+    HOUGH_PHASE(HOUGH_PHASE_SCAN);
 
     // 4. raster-order positions and peak records: keys (column, group of key_words bitmap words)
     // in raster order, counted from the peak bitmap
@@ -1343,6 +1354,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     }
     __syncthreads();
     total = block_exscan(cnt, nkeys, sh.tmp);
+    HOUGH_PHASE(HOUGH_PHASE_EXSCAN);
     // peaks of the tile's low columns (mirror-pair tiles: the high columns follow them)
     n_low = (pl.mp && Wd < wt) ? cnt[Wd << pl.key_shift] : total;
     // event column of tile-local column c: mirror-pair tiles hold [aw, aw + Wd) then
@@ -1405,6 +1417,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     }
     cs_tile = do_cs ? block_sum_u64(csum, sh.red) : 0ull;
     __syncthreads();
+    HOUGH_PHASE(HOUGH_PHASE_RECORDS);
   }
 
   // 5. tiles: publish, and let the last tile of the event merge
@@ -1469,6 +1482,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     if (too_large) sh.flags |= HOUGH_F_EVENT_TOO_LARGE;
   }
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_MERGE);
   int kept = 0;
   if (too_large) {
     for (long long i = tid; i < nll; i += bd) io.mask[a + i] = 0;
@@ -1482,6 +1496,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(kFull, kept, o);
   if (lane == 0 && kept) atomicAdd(&sh.kept_tot, kept);
   __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_SEL_B);
   if (tid == 0) {
     io.nkept[e] = sh.kept_tot;
     if (sh.flags) atomicOr(io.status, sh.flags);
@@ -1660,3 +1675,28 @@ cudaError_t launch_fused(const Plan& pl, const FusedIO& io, const TrigTable& tri
 }
 
 }  // namespace hgpu
+
+extern "C" int hough_phase_cycles(uint64_t* host_cycles, int32_t n, int32_t reset, int32_t* enabled) {
+  if (!host_cycles || n < 0) return HOUGH_EINVAL;
+  const int m = n < HOUGH_PHASE_COUNT ? n : HOUGH_PHASE_COUNT;
+#ifdef HOUGH_PHASE_TIMERS
+  if (enabled) *enabled = 1;
+  unsigned long long buf[HOUGH_PHASE_COUNT];
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(buf, hgpu::g_phase_cycles, sizeof(buf));
+  if (e == cudaSuccess && reset) {
+    const unsigned long long zero[HOUGH_PHASE_COUNT] = {};
+    e = cudaMemcpyToSymbol(hgpu::g_phase_cycles, zero, sizeof(zero));
+  }
+  if (e != cudaSuccess) {
+    hgpu::note_cuda_error(e);
+    return HOUGH_ECUDA;
+  }
+  for (int i = 0; i < m; ++i) host_cycles[i] = buf[i];
+#else
+  (void)reset;
+  if (enabled) *enabled = 0;
+  for (int i = 0; i < m; ++i) host_cycles[i] = 0;
+#endif
+  return HOUGH_OK;
+}

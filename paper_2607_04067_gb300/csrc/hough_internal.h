@@ -104,4 +104,7 @@ cudaError_t launch_selftest_bin(int n_rho, long long lo, long long hi, unsigned 
 cudaError_t launch_probe_atomics(int mode, int ctas_per_sm, int threads, int smem_bytes, int iters,
                                  unsigned long long* sink, cudaStream_t st);
 
+// Records a CUDA error for hough_last_cuda_error (this host thread).
+void note_cuda_error(cudaError_t e);
+
 }  // namespace hgpu

@@ -24,7 +24,6 @@
 namespace hgpu {
 
 int make_plan(const hough_params* p, Plan& pl, int acc32);
-void note_cuda_error(cudaError_t e);
 
 namespace {
 

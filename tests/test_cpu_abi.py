@@ -84,3 +84,19 @@ def test_bin_magic_exact_at_every_bin_edge():
             for t in (edge - 2, edge - 1, edge, edge + 1):
                 if 0 <= t < two_h:
                     assert (t * M) >> 64 == (t * n) // two_h
+
+
+def test_phase_counters_off_in_the_default_build(lib):
+    """hough_phase_cycles needs no GPU in the default build: it reports the timers as off and
+    writes zeros; bad arguments are refused."""
+    enabled, cyc = h.phase_cycles(reset=True)
+    assert enabled is False and set(cyc) == set(h.PHASES) and not any(cyc.values())
+    assert lib.hough_phase_cycles(None, 4, 0, None) == -1
+    buf = (ctypes.c_uint64 * 4)()
+    assert lib.hough_phase_cycles(buf, -1, 0, None) == -1
+    # the header's phase numbering is the binding's
+    with open(h.HEADER) as f:
+        text = f.read()
+    ids = dict((m.group(1).lower(), int(m.group(2))) for m in re.finditer(r"#define HOUGH_PHASE_(\w+) (\d+)", text))
+    assert ids.pop("count") == len(h.PHASES)
+    assert [name for name, _ in sorted(ids.items(), key=lambda kv: kv[1])] == list(h.PHASES)
