@@ -503,13 +503,21 @@ static int enqueue_batched(const Common& cm0, const hough_params* p, int64_t n_h
 
 namespace {
 
+// Everything but the launch shape that the work depends on, so that a cached shape is reused
+// only for the same kind of work (the peak finder included).
 struct TuneKey {
-  int n_theta, n_rho, threshold, keep_hw, max_peaks, device, sms, hits_bucket;
+  int n_theta, n_rho, threshold, keep_hw, max_peaks, peak_mode, rel_num, rel_den, nms_radius, device, sms,
+      hits_bucket;
   bool operator<(const TuneKey& o) const { return std::memcmp(this, &o, sizeof(TuneKey)) < 0; }
 };
 
+// The launch shape the autotuner picks; the rest of the caller's parameters is left alone.
+struct TuneShape {
+  int theta_tiles, events_per_cta, block;
+};
+
 std::mutex g_tune_mu;
-std::map<TuneKey, hough_params> g_tune_cache;
+std::map<TuneKey, TuneShape> g_tune_cache;
 
 struct TuneScratch {
   size_t npeaks, peaks, mask, nkept, ws, total;
@@ -562,6 +570,10 @@ int hough_autotune(hough_params* p, const int32_t* d_xy, int64_t n_hits, const i
   key.threshold = p->threshold;
   key.keep_hw = p->keep_halfwidth;
   key.max_peaks = p->max_peaks;
+  key.peak_mode = p->peak_mode;
+  key.rel_num = p->peak_mode == HOUGH_PEAK_ITERATIVE ? p->rel_num : 0;
+  key.rel_den = p->peak_mode == HOUGH_PEAK_ITERATIVE ? p->rel_den : 0;
+  key.nms_radius = p->peak_mode == HOUGH_PEAK_ITERATIVE ? p->nms_radius : 0;
   cudaGetDevice(&key.device);
   cudaDeviceGetAttribute(&key.sms, cudaDevAttrMultiProcessorCount, key.device);
   {
@@ -574,7 +586,9 @@ int hough_autotune(hough_params* p, const int32_t* d_xy, int64_t n_hits, const i
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      *p = it->second;
+      p->theta_tiles = it->second.theta_tiles;
+      p->events_per_cta = it->second.events_per_cta;
+      p->block = it->second.block;
       if (best_ms) *best_ms = -1.0f;
       return HOUGH_OK;
     }
@@ -631,9 +645,11 @@ int hough_autotune(hough_params* p, const int32_t* d_xy, int64_t n_hits, const i
   if (!found) return HOUGH_ESMEM;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best;
+    g_tune_cache[key] = TuneShape{best.theta_tiles, best.events_per_cta, best.block};
   }
-  *p = best;
+  p->theta_tiles = best.theta_tiles;
+  p->events_per_cta = best.events_per_cta;
+  p->block = best.block;
   if (best_ms) *best_ms = best_t;
   return HOUGH_OK;
 }

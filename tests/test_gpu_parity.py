@@ -148,6 +148,35 @@ def test_full_size_sampled(h, name, sample):
     assert np.array_equal(csum[ev.off[1:]] - csum[ev.off[:-1]], nk)
     assert np.all(to_np(out.npeaks) <= cfg.max_peaks)
     assert set(np.unique(m)) <= {0, 1}
+    # the shape the benchmark times: tuned on the first 10,000 events, whole batch again
+    ns = min(ev.n_events, 10000)
+    pt, _ = h.autotune(xy[: int(ev.off[ns])], off[: ns + 1], p)
+    out2 = h.run(xy, off, pt, checksum=False, batched=True)
+    assert h.status(out2.status) == 0
+    assert torch.equal(out2.npeaks, out.npeaks) and torch.equal(out2.nkept, out.nkept)
+    assert torch.equal(out2.mask, out.mask) and torch.equal(out2.peaks, out.peaks)
+
+
+def test_full_size_sampled_iterative(h):
+    """The batched workload (100,000 events) with the paper's iterative finder in the
+    benchmark's configuration (half the maximum, radius 3, autotuned shape); the oracle
+    recomputes a random sample of events one by one."""
+    cfg = gen.CONFIGS["batched"]
+    ev = gen.generate(cfg, with_truth=False)
+    xy, off = dev(ev)
+    kw = dict(peak_mode=1, rel_num=1, rel_den=2, nms_radius=3)
+    p = cfg_params(h, cfg, **kw)
+    p, _ = h.autotune(xy[: int(ev.off[10000])], off[:10001], p)
+    out = h.run(xy, off, p, checksum=False, batched=True)
+    assert h.status(out.status) == 0
+    rng = np.random.default_rng(2)
+    events = np.sort(rng.choice(ev.n_events, size=120, replace=False))
+    events[0] = 0
+    events[-1] = ev.n_events - 1
+    sxy, soff = sub_batch(ev.xy, ev.off, events)
+    ref = oracle.run(sxy, soff, oracle.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth,
+                                              cfg.max_peaks, **kw), threads=THREADS)
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, events=events)
 
 
 # ---------------------------------------------------------------- edge cases
@@ -335,6 +364,33 @@ def test_autotuned_shape_gives_identical_results(h):
     out = h.run(xy, off, tuned, checksum=True, batched=True)
     assert h.status(out.status) == 0
     assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, checksum=out.checksum)
+
+
+def test_autotune_cache_keys_the_peak_finder(h):
+    """The autotuner writes only the launch shape, and its cache tells the peak finders apart:
+    tuning the 3x3 finder first must not hand the iterative finder's tuning the 3x3 parameters.
+    (Threshold 17 is used by no other test, so both keys are new to this process.)"""
+    cfg = gen.CONFIGS["plain_paper"]
+    ev = gen.generate(cfg, 300)
+    xy, off = dev(ev)
+    algo = ("n_theta", "n_rho", "threshold", "keep_halfwidth", "max_peaks", "peak_mode", "rel_num", "rel_den",
+            "nms_radius")
+    p0 = h.params(cfg.n_theta, cfg.n_rho, 17, cfg.keep_halfwidth, 512)
+    t0, ms0 = h.autotune(xy, off, p0)
+    assert ms0 > 0 and [getattr(t0, f) for f in algo] == [getattr(p0, f) for f in algo]
+    p1 = h.params(cfg.n_theta, cfg.n_rho, 17, cfg.keep_halfwidth, 512, peak_mode=1, rel_num=1, rel_den=2,
+                  nms_radius=3)
+    t1, ms1 = h.autotune(xy, off, p1)
+    assert ms1 > 0, "the iterative finder's tuning came from the 3x3 finder's cache entry"
+    assert [getattr(t1, f) for f in algo] == [getattr(p1, f) for f in algo]
+    t1b, ms1b = h.autotune(xy, off, p1)
+    assert ms1b == -1.0 and [getattr(t1b, f) for f, _ in t1b._fields_] == [getattr(t1, f) for f, _ in t1._fields_]
+    op = oracle.params(cfg.n_theta, cfg.n_rho, 17, cfg.keep_halfwidth, 512, peak_mode=1, rel_num=1, rel_den=2,
+                       nms_radius=3)
+    ref = oracle.run(ev.xy, ev.off, op, threads=THREADS)
+    out = h.run(xy, off, t1, batched=True)
+    assert h.status(out.status) == ref.status
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off)
 
 
 def test_host_errors(h):
