@@ -548,14 +548,18 @@ def test_iterative_stepwise_large_accumulator(h):
 
 # ---------------------------------------------------------------- host-buffer path (pipelined chunks)
 
-@pytest.mark.parametrize("name,n", [("plain_paper", 300), ("batched", 9000), ("stress", 4100)])
-def test_host_path_matches_oracle(h, name, n):
-    """hough_run_host: pinned host inputs in, host results out. 9,000 and 4,100 events run as
-    several pipelined chunks (rebased offsets, peaks packed per chunk and re-based on the host)."""
+@pytest.mark.parametrize("name,n,iterative", [("plain_paper", 300, False), ("batched", 9000, False),
+                                               ("stress", 4100, False), ("batched", 5000, True)])
+def test_host_path_matches_oracle(h, name, n, iterative):
+    """hough_run_host: pinned host inputs in, host results out. 9,000, 5,000 and 4,100 events run
+    as several pipelined chunks (rebased offsets, peaks packed per chunk and re-based on the
+    host); also with the iterative finder (half the maximum, radius 3)."""
     cfg = gen.CONFIGS[name]
     ev = gen.generate(cfg, n)
-    ref = oracle_of(cfg, ev)
-    p = cfg_params(h, cfg)
+    kw = dict(peak_mode=1, rel_num=1, rel_den=2, nms_radius=3) if iterative else {}
+    ref = oracle.run(ev.xy, ev.off, oracle.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth,
+                                                  cfg.max_peaks, **kw), threads=THREADS)
+    p = cfg_params(h, cfg, **kw)
     r = h.HostRunner(ev.n_hits, ev.n_events, p)
     xy = torch.from_numpy(ev.xy).pin_memory()
     off = torch.from_numpy(ev.off).pin_memory()
