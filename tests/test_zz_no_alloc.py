@@ -35,13 +35,15 @@ def same(h, a, b):
         assert np.array_equal(pa[e, :n], pb[e, :n]), e
 
 
-@pytest.mark.parametrize("name,n,tiles,max_peaks", [("plain_paper", 300, 0, 2048), ("plain_paper", 60, 2, 512),
-                                                    ("plain_small", 100, 0, 1024)])
-def test_static_scratch_matches_workspace_path_twice(h, name, n, tiles, max_peaks):
+@pytest.mark.parametrize("name,n,tiles,max_peaks,iterative",
+                         [("plain_paper", 300, 0, 2048, False), ("plain_paper", 60, 2, 512, False),
+                          ("plain_small", 100, 0, 1024, False), ("plain_paper", 300, 0, 2048, True)])
+def test_static_scratch_matches_workspace_path_twice(h, name, n, tiles, max_peaks, iterative):
     cfg = gen.CONFIGS[name]
     ev = gen.generate(cfg, n)
     xy, off = torch.from_numpy(ev.xy).cuda(), torch.from_numpy(ev.off).cuda()
-    p = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, max_peaks, theta_tiles=tiles)
+    kw = dict(peak_mode=1, rel_num=1, rel_den=2, nms_radius=3) if iterative else {}
+    p = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, max_peaks, theta_tiles=tiles, **kw)
     assert h.workspace_size(p, ev.n_events) <= 32 * 1024 * 1024
     ref = h.run(xy, off, p, checksum=True, batched=True)
     for _ in range(2):  # the array keeps the previous call's contents; results must not depend on them
