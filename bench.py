@@ -137,6 +137,12 @@ def peak_args(args):
     return 1, num, den, args.nms_radius
 
 
+def peak_finder_name(args) -> str:
+    if getattr(args, "peak_mode", "local-max") != "iterative":
+        return "3x3 local maxima"
+    return f"iterative, relative threshold {args.rel} of the maximum, suppression radius {args.nms_radius}"
+
+
 def oracle_baseline(cfg, ev, budget_events: int, threads: int, peak=(0, 0, 1, 1)):
     """The CPU oracle as it stands, timed on the host cores over the first events of the batch."""
     import oracle
@@ -157,7 +163,7 @@ def run_reference(args, cfg):
     threads = os.cpu_count() or 1
     per_step = args.ref_events
     ev = gen.generate(cfg, per_step, with_truth=False)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
+    for _ in range(max(0, args.warmup)):
         oracle_baseline(cfg, ev, per_step, threads, peak_args(args))
     times = []
     for _ in range(args.steps):
@@ -171,7 +177,7 @@ def run_reference(args, cfg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": cfg.name, "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
-                   "events_per_step": per_step},
+                   "peak_finder": peak_finder_name(args), "events_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -572,9 +578,7 @@ def main():
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": cfg.name, "events_per_gpu": n_events, "hits_per_gpu": ev.n_hits,
                    "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
-                   "peak_finder": ("3x3 local maxima" if args.peak_mode == "local-max" else
-                                   f"iterative, relative threshold {args.rel} of the maximum, "
-                                   f"suppression radius {args.nms_radius}"),
+                   "peak_finder": peak_finder_name(args),
                    "max_peaks": cfg.max_peaks, "launch": {"theta_tiles": plan.theta_tiles, "block": plan.block,
                                                           "events_per_cta": plan.events_per_cta,
                                                           "autotuned": not (args.no_tune or args.shape),

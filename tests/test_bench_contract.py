@@ -23,6 +23,7 @@ def test_reference_arm_json_line(extra):
     assert d["unit"] == "events/s" and d["higher_is_better"] is True and d["data"] == "synthetic"
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["config"]["workload"] == "plain_small"
+    assert d["config"]["peak_finder"].startswith("iterative" if extra else "3x3")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = d["e2e"]
