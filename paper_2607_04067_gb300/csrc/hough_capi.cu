@@ -271,7 +271,7 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       pl.key_shift = ks;
       pl.key_words = gw;
     }
-    // the most staged hits, then (iterative finder) the most candidate keys of its sorted form
+    // the most staged hits, then (iterative finder) the most candidate keys of its candidate form
     for (int cap = 4096; cap >= 512; cap >>= 1) {
       pl.hit_cap = cap;
       const int icap0 = pl.peak_mode == HOUGH_PEAK_ITERATIVE ? 8192 : 0;

@@ -17,7 +17,7 @@ constexpr int kIterSliceRows = 32;
 struct Plan {
   int n_theta, n_rho, threshold, keep_hw, max_peaks;
   int peak_mode, rel_num, rel_den, nms_radius;  // peak finder (0: 3x3 local maxima, 1: iterative)
-  int iter_cap;   // iterative finder: candidate keys of its sorted form (0: one pass per peak only)
+  int iter_cap;   // iterative finder: candidate keys of its candidate form (0: one pass per peak only)
   int tiles;      // theta tiles per event
   int tile_w;     // columns per tile (last tile may be narrower)
   int groups;     // 32-column groups per tile

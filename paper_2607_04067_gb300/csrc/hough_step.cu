@@ -316,7 +316,7 @@ __global__ void peaks_iterative_kernel(const int16_t* __restrict__ acc, int NT, 
   extern __shared__ uint32_t sm[];
   __shared__ int s_sel[8];
   const long long e = blockIdx.x;
-  // the finder's scratch, then the suppression bitmap (also the sorted form's bitmap)
+  // the finder's scratch, then the suppression bitmap (also the candidate walk's bitmap)
   const int sw = iter_scratch_words(NT, NR, SH);
   uint32_t* cm = sm;
   uint32_t* gone = sm + (sw > cap ? sw : cap);
@@ -369,7 +369,7 @@ cudaError_t launch_peaks(const int16_t* acc, long long n_events, const hough_par
   if (n_events == 0) return cudaSuccess;
   if (p.peak_mode == HOUGH_PEAK_ITERATIVE) {
     // slices of 32 rows, or taller ones where the maxima and the suppression bitmap would not
-    // fit in shared memory; then as many candidate keys for the sorted form as the rest holds
+    // fit in shared memory; then as many candidate keys for the candidate form as the rest holds
     const int nwords = (p.n_theta * p.n_rho + 31) / 32, budget = 200 * 1024 / 4;
     int SH = 32;
     while (iter_scratch_words(p.n_theta, p.n_rho, SH) + nwords > budget) SH *= 2;
