@@ -925,7 +925,7 @@ int hough_selftest_bin(int32_t n_rho, int64_t rho_lo, int64_t rho_hi, unsigned l
 
 int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t n_samples, unsigned long long* d_out,
                          void* stream) {
-  hough_params p{n_theta, n_rho, 1, 1, 1, 0, 0, 0};
+  hough_params p{n_theta, n_rho, 1, 1, 1, 0, 0, 0, HOUGH_PEAK_LOCAL_MAX, 0, 1, 0};
   Plan pl;
   if (!d_out || n_samples < 0 || make_plan(&p, pl) != HOUGH_OK) return HOUGH_EINVAL;
   mp_consts(pl, n_rho);  // the mirror-pair estimate is checked whatever layout the plan chose
