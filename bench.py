@@ -205,9 +205,10 @@ def probe_atomic_ceiling(h, torch, stream):
     return out
 
 
-def measure_serving(h, cfg, p, rates, seconds, pool_events=20000, seed=11):
-    """Continuous-batching server vs plain per-batch launches of 1,000 events on the same Poisson
-    arrival streams. Latency runs from each event's scheduled arrival to its results in host memory."""
+def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000, seed=11):
+    """Continuous-batching server (4 slots, micro-batches of at most 256 events, launched after
+    flush_us) vs plain per-batch launches of 1,000 events on the same Poisson arrival streams.
+    Latency runs from each event's scheduled arrival to its results in host memory."""
     pool = gen.generate(cfg, pool_events, with_truth=False)
     rng = np.random.default_rng(seed)
     out = []
@@ -215,7 +216,8 @@ def measure_serving(h, cfg, p, rates, seconds, pool_events=20000, seed=11):
         n = int(rate * seconds)
         arrival = np.cumsum(rng.exponential(1e9 / rate, size=n)).astype(np.int64)
         row = {"offered_events_per_s": rate, "seconds": seconds, "events": n}
-        for name, kw in (("served", dict(slots=4, max_batch_events=256, flush_us=200.0)),
+        row["flush_us"] = flush_us
+        for name, kw in (("served", dict(slots=4, max_batch_events=256, flush_us=flush_us)),
                          ("plain_1000", dict(slots=1, max_batch_events=1000, flush_us=0.0))):
             with h.Server(p, max_batch_hits=1 << 22, **kw) as srv:
                 t0 = srv.replay(pool.xy, pool.off, arrival)
@@ -413,9 +415,11 @@ def main():
     ap.add_argument("--ref-events", type=int, default=3000, help="oracle events per reference step")
     ap.add_argument("--cpu-sample", type=int, default=10000,
                     help="oracle events for cpu_baseline (a tenth of them for the single-thread run)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each serving stream")
+    ap.add_argument("--serve-flush-us", type=float, default=50.0,
+                    help="serving loop: longest wait of a request before its partial micro-batch is launched")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
@@ -519,7 +523,8 @@ def main():
     off_h = torch.from_numpy(ev.off).pin_memory()
     stored = int(out.npeaks.clamp(max=cfg.max_peaks).sum().item())
     runner = h.HostRunner(ev.n_hits, ev.n_events, p, peaks_cap=stored + stored // 8 + 1024)
-    runner(xy_h, off_h, stream)
+    for _ in range(2):  # graphs, streams and host pages warm
+        runner(xy_h, off_h, stream)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -568,7 +573,8 @@ def main():
     if not args.no_serve:
         scfg = gen.CONFIGS["served"]
         served = measure_serving(h, scfg, h.params(scfg.n_theta, scfg.n_rho, scfg.threshold, scfg.keep_halfwidth,
-                                                   scfg.max_peaks), (50_000, 200_000, 400_000), args.serve_seconds)
+                                                   scfg.max_peaks), (50_000, 200_000, 400_000), args.serve_seconds,
+                                 args.serve_flush_us)
 
     import oracle
     rc, rs = oracle.metrics(out.mask.cpu().numpy(), ev.truth) if ev.truth is not None else (None, None)

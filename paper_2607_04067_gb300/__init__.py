@@ -385,7 +385,7 @@ class Server:
     torch tensors owned by this object; the loop itself is a native thread in the library."""
 
     def __init__(self, p: Params, slots: int = 4, max_batch_events: int = 256, max_batch_hits: int = 1 << 20,
-                 flush_us: float = 200.0, queue_capacity: int = 1 << 20, device="cuda"):
+                 flush_us: float = 50.0, queue_capacity: int = 1 << 20, device="cuda"):
         torch = _torch()
         self.cfg = ServeConfig(p, slots, max_batch_events, max_batch_hits, int(flush_us * 1000), queue_capacity, 0)
         lib = load()
