@@ -141,7 +141,8 @@ __host__ __device__ inline int iter_scratch_words(int NT, int NR, int SH) {
 // Iterative peak extraction (the paper's finder, Sec. 2), one pass per peak, over an
 // accumulator behind `cells` (get(j, k) -> votes of a cell not yet suppressed, 0 once
 // suppressed; clear(j, k) suppresses one cell without touching any other cell's value, so that
-// other lanes may read and clear other cells meanwhile). The general form of the finder, taken
+// other lanes may read and clear other cells meanwhile; with kPairs true, word(w, k) is the
+// 32-bit word of columns w (low half) and NT - 1 - w (high half) at row k, NT even). The general form of the finder, taken
 // when the sorted form below does not apply.
 // Cells are ordered by the packed word (votes << 16) | (n_rho - 1 - k): within a column the
 // larger word is the cell with more votes and, on equal votes, the smaller k. Across columns
@@ -349,11 +350,20 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
     s[1] = 0;
   }
   __syncthreads();
-  // the maximum (a warp takes rows, its lanes consecutive columns)
+  // the maximum (a warp takes rows, its lanes consecutive columns, or with Cells::kPairs
+  // consecutive words of two columns each: w and NT - 1 - w)
   {
     int m = 0;
-    for (int k = warp; k < NR; k += nwarps)
-      for (int j = lane; j < NT; j += 32) m = max(m, cells.get(j, k));
+    if constexpr (Cells::kPairs) {
+      for (int k = warp; k < NR; k += nwarps)
+        for (int w = lane; w < (NT >> 1); w += 32) {
+          const uint32_t x = cells.word(w, k);
+          m = max(m, (int)max(x & 0xffffu, x >> 16));
+        }
+    } else {
+      for (int k = warp; k < NR; k += nwarps)
+        for (int j = lane; j < NT; j += 32) m = max(m, cells.get(j, k));
+    }
     m = __reduce_max_sync(0xffffffffu, m);
     if (lane == 0 && m) atomicMax(&s[0], m);
   }
@@ -364,18 +374,43 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
   const long long need = ((long long)rel_num * amax + rel_den - 1) / rel_den;
   const int tq = (int)max((long long)thr, need);
   *tq_out = tq;
-  for (int k = warp; k < NR; k += nwarps) {
-    for (int j0 = 0; j0 < NT; j0 += 32) {
-      const int j = j0 + lane;
-      const int v = j < NT ? cells.get(j, k) : 0;
-      const bool c = v >= tq;
-      const uint32_t bal = __ballot_sync(0xffffffffu, c);
-      if (bal) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&s[1], __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const int pos = base + __popc(bal & ((1u << lane) - 1u));
-        if (c && pos < cap) keys[pos] = ((uint32_t)v << 20) | ((uint32_t)(1023 - j) << 10) | (uint32_t)(1023 - k);
+  auto key_of = [&](int v, int j, int k) {
+    return ((uint32_t)v << 20) | ((uint32_t)(1023 - j) << 10) | (uint32_t)(1023 - k);
+  };
+  if constexpr (Cells::kPairs) {
+    const int Wd = NT >> 1;
+    for (int k = warp; k < NR; k += nwarps) {
+      for (int w0 = 0; w0 < Wd; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t x = w < Wd ? cells.word(w, k) : 0u;
+        const int vl = (int)(x & 0xffffu), vh = (int)(x >> 16);
+        const bool cl = w < Wd && vl >= tq, ch = w < Wd && vh >= tq;
+        const uint32_t bl = __ballot_sync(0xffffffffu, cl), bh = __ballot_sync(0xffffffffu, ch);
+        if (bl | bh) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s[1], __popc(bl) + __popc(bh));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          const uint32_t lt = (1u << lane) - 1u;
+          const int pl = base + __popc(bl & lt), ph = base + __popc(bl) + __popc(bh & lt);
+          if (cl && pl < cap) keys[pl] = key_of(vl, w, k);
+          if (ch && ph < cap) keys[ph] = key_of(vh, NT - 1 - w, k);
+        }
+      }
+    }
+  } else {
+    for (int k = warp; k < NR; k += nwarps) {
+      for (int j0 = 0; j0 < NT; j0 += 32) {
+        const int j = j0 + lane;
+        const int v = j < NT ? cells.get(j, k) : 0;
+        const bool c = v >= tq;
+        const uint32_t bal = __ballot_sync(0xffffffffu, c);
+        if (bal) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s[1], __popc(bal));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          const int pos = base + __popc(bal & ((1u << lane) - 1u));
+          if (c && pos < cap) keys[pos] = key_of(v, j, k);
+        }
       }
     }
   }

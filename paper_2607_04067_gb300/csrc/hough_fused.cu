@@ -389,8 +389,10 @@ __device__ __forceinline__ int mp_get(const uint32_t* acc, int c, int k, int Wd,
 // leaves the other half of the word alone.
 template <bool A32, bool MP>
 struct FusedCells {
+  static constexpr bool kPairs = MP;  // word w holds columns w and 2 Wd - 1 - w
   uint32_t* acc;
   int Wd, nrp, rp;  // tile words, padded rows (other layouts), rows with guards (mirror-pair)
+  __device__ uint32_t word(int w, int k) const { return acc[mp_word(w, k + 1, rp)]; }
   __device__ int get(int j, int k) const {
     if (MP) {
       const bool hi = j >= Wd;

@@ -297,6 +297,7 @@ __global__ void circles_kernel(const int* __restrict__ npeaks, const hough_peak*
 // The iterative finder on an accumulator in HBM (read only): suppressed cells are kept in a
 // shared-memory bitmap, one CTA per event.
 struct GlobalCells {
+  static constexpr bool kPairs = false;
   const int16_t* A;
   uint32_t* gone;
   int NR;
