@@ -543,6 +543,57 @@ def test_iterative_matches_greedy_restatement(seed):
     assert [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk] == exp
 
 
+def _rounds_peaks(acc, T, num, den, R):
+    """The kept set reached by rounds of local rules (no ordering of the work): a candidate
+    (cell passing the thresholds) is dropped once a kept candidate lies in its window, and kept
+    once every higher-ranked candidate in its window is dropped; rank is (votes desc, raster
+    asc). Each round applies the rules to every undecided candidate on the states of the round
+    before. The kept cells, listed in rank order."""
+    NT, NR = acc.shape
+    amax = int(acc.max()) if acc.size else 0
+    cand = [(j, k) for j in range(NT) for k in range(NR) if acc[j, k] >= T and int(acc[j, k]) * den >= num * amax]
+    rank = {c: (-int(acc[c]), c[0] * NR + c[1]) for c in cand}
+    window = {c: [d for d in cand if d != c and _in_window(c, d, R, NT, NR)] for c in cand}
+    state = {c: 0 for c in cand}  # 0 undecided, 1 dropped, 2 kept
+    for _ in range(len(cand) + 1):
+        new = dict(state)
+        for c in cand:
+            if state[c]:
+                continue
+            if any(state[d] == 2 for d in window[c]):
+                new[c] = 1
+            elif all(state[d] == 1 for d in window[c] if rank[d] < rank[c]):
+                new[c] = 2
+        if new == state:
+            break
+        state = new
+    assert all(state.values()), "every candidate is decided"
+    kept = sorted((c for c in cand if state[c] == 2), key=lambda c: rank[c])
+    return [(c, int(acc[c])) for c in kept]
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_iterative_local_rules_reach_the_greedy_list(seed):
+    """The GPU decides the kept set by the local rules of _rounds_peaks (a kept cell in the
+    window of an undecided candidate drops it; a candidate whose higher-ranked window cells are
+    all dropped is kept). The window relation is symmetric (checked here too), so these rules
+    reach exactly the oracle's extraction list, ties and theta wrap included."""
+    rng = np.random.default_rng(100 + seed)
+    NT, NR = int(rng.choice([4, 6, 8, 12])), int(rng.choice([4, 5, 8, 11]))
+    acc = rng.integers(0, int(rng.choice([3, 6, 12])), size=(NT, NR)).astype(np.int16)
+    T, num, den = int(rng.integers(1, 3)), int(rng.integers(0, 3)), 4
+    R = int(rng.integers(0, (NT - 1) // 2 + 1))
+    cells = [(j, k) for j in range(NT) for k in range(NR)]
+    for a in cells[::3]:
+        for b in cells[::2]:
+            assert _in_window(a, b, R, NT, NR) == _in_window(b, a, R, NT, NR)
+    p = oracle.params(NT, NR, T, 1, 1000, peak_mode=oracle.PEAK_ITERATIVE, rel_num=num, rel_den=den, nms_radius=R)
+    n, pk = oracle.peaks_iterative(acc, p)
+    got = _rounds_peaks(acc, T, num, den, R)
+    assert n == len(got)
+    assert [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk] == got
+
+
 def test_iterative_hand_cases():
     NT, NR = 8, 8
     acc = np.zeros((NT, NR), np.int16)
