@@ -100,3 +100,19 @@ def test_phase_counters_off_in_the_default_build(lib):
     ids = dict((m.group(1).lower(), int(m.group(2))) for m in re.finditer(r"#define HOUGH_PHASE_(\w+) (\d+)", text))
     assert ids.pop("count") == len(h.PHASES)
     assert [name for name, _ in sorted(ids.items(), key=lambda kv: kv[1])] == list(h.PHASES)
+
+
+@pytest.mark.parametrize("nt", [4, 8, 64, 100, 256, 300, 512, 1000, 1024])
+@pytest.mark.parametrize("nr", [4, 63, 256, 1000, 1024])
+def test_plans_over_shapes(nt, nr):
+    """Every accumulator shape has a 3x3-finder plan (theta-tiled where one CTA cannot hold it).
+    The iterative finder needs the whole accumulator in one CTA: it plans untiled, or is refused
+    with HOUGH_ESMEM (the stepwise hough_peaks takes those shapes); up to 256 x 256 it fits."""
+    r = h.resolve(h.params(nt, nr, 16, 1, 1024))
+    assert r.theta_tiles >= 1 and r.block % 32 == 0 and 32 <= r.block <= 1024 and r.events_per_cta >= 1
+    q = h.params(nt, nr, 16, 1, 1024, peak_mode=h.PEAK_ITERATIVE, rel_num=1, rel_den=2, nms_radius=1)
+    try:
+        ri = h.resolve(q)
+        assert ri.theta_tiles == 1 and ri.block % 32 == 0
+    except h.HoughError as e:
+        assert e.code == -3 and nt * nr > 256 * 256
