@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 import gen  # noqa: E402
 
 METRIC = "events/s and p99 event latency on 1 GB300 (batched/served vs plain), bit-exact"
-OPS_PER_VOTE = 8  # 2 multiply-adds (rho), 2 clamps, 2 multiplies (exact bin division), 1 address, 1 shared add
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_kernel_batched_traffic.txt")
+PEAK_RECORD_BYTES = 8
 KERNEL_SOURCES = ["paper_2607_04067_gb300/csrc/hough_fused.cu", "paper_2607_04067_gb300/csrc/hough_device.cuh"]
 
 
@@ -129,6 +129,13 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def workload_config(cfg, n_events, args):
+    """The workload a line is measured on: identical in the GPU arm and the reference arm."""
+    return {"workload": cfg.name, "events_per_gpu": n_events, "n_theta": cfg.n_theta, "n_rho": cfg.n_rho,
+            "threshold": cfg.threshold, "keep_halfwidth": cfg.keep_halfwidth, "max_peaks": cfg.max_peaks,
+            "peak_finder": peak_finder_name(args), "parallelism": "events sharded over ranks, no collective"}
+
+
 def peak_args(args):
     """(peak_mode, rel_num, rel_den, nms_radius) of the command line."""
     if getattr(args, "peak_mode", "local-max") != "iterative":
@@ -171,13 +178,14 @@ def run_reference(args, cfg):
         times.append(dt)
     total = sum(times)
     value = per_step * args.steps / total
-    sample = f"{per_step} events of the {cfg.name} workload per step (first events of the seeded batch)"
+    sample = (f"{per_step} events of the {cfg.name} workload per step (the first events of its seeded batch), "
+              f"timed on {threads} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": cfg.name, "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
-                   "peak_finder": peak_finder_name(args), "events_per_step": per_step},
+        "config": workload_config(cfg, args.events or cfg.n_events, args),
+        "sample": {"events_per_step": per_step, "note": "the oracle times a bounded sample of the workload"},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -188,7 +196,7 @@ def probe_atomic_ceiling(h, torch, stream):
     out = {}
     sink = torch.zeros(1, dtype=torch.int64, device="cuda")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    for mode, name in ((0, "lane_bank"), (1, "random_word")):
+    for mode, name in ((0, "lane_bank"), (4, "lane_bank_random_rows"), (1, "random_word")):
         ctas, threads, smem, iters = 2, 1024, 96 * 1024, 400
         for _ in range(2):
             h.probe_smem_atomics(mode, ctas, threads, smem, iters, sink, stream)
@@ -205,31 +213,67 @@ def probe_atomic_ceiling(h, torch, stream):
     return out
 
 
-def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000, seed=11):
+def serve_stream(h, p, kw, pool, arrival, max_batch_hits=1 << 22):
+    """One arrival stream through a server configured by kw: sustained events/s (completed over
+    the span from the first scheduled arrival to the last result), latency percentiles from
+    scheduled arrival to results in host memory, device flags, and the loop's stall watch."""
+    with h.Server(p, max_batch_hits=max_batch_hits, **kw) as srv:
+        t0 = srv.replay(pool.xy, pool.off, arrival)
+        srv.drain(300)
+        res = srv.poll_numpy(len(arrival) + 16)
+        stats, rec = srv.trace()
+    lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e3
+    span = (res["t_done_ns"].max() - t0) / 1e9 if len(res) else float("nan")
+    out = {"sustained_events_per_s": len(res) / span, "p50_us": float(np.percentile(lat, 50)),
+           "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
+           "completed": int(len(res)), "flags": int(np.bitwise_or.reduce(res["status"])),
+           "batches": stats["batches"], "mean_batch_events": float(rec["n_events"].mean()) if len(rec) else None,
+           "loop_stalls": stats["loop_stalls"], "loop_max_gap_us": stats["loop_max_gap_ns"] / 1e3,
+           "loop_max_gap_cpu_us": stats["loop_max_gap_cpu_ns"] / 1e3, "submit_stalls": stats["submit_stalls"],
+           "submit_max_late_us": stats["submit_max_late_ns"] / 1e3,
+           "submit_max_late_cpu_us": stats["submit_max_late_cpu_ns"] / 1e3}
+    if len(rec):  # where a micro-batch's time goes (medians over the stream's most recent batches)
+        out["batch_us"] = {"gather_and_enqueue": float(np.median(rec["t_launched"] - rec["t_gather"]) / 1e3),
+                           "device_and_copies": float(np.median(rec["t_done_seen"] - rec["t_launched"]) / 1e3),
+                           "results_to_callers": float(np.median(rec["t_finished"] - rec["t_done_seen"]) / 1e3)}
+    return out
+
+
+SERVED = dict(slots=4, max_batch_events=256, flush_us=50.0)
+PLAIN_1000 = dict(slots=1, max_batch_events=1000, flush_us=0.0)
+
+
+def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000, seed=11, sat_events=400_000,
+                    sat_rates=(1_000_000, 2_000_000, 4_000_000), sat_seconds=0.5):
     """Continuous-batching server (4 slots, micro-batches of at most 256 events, launched after
-    flush_us) vs plain per-batch launches of 1,000 events on the same Poisson arrival streams.
+    flush_us) vs plain per-batch launches of 1,000 events (one batch in flight, launched when
+    full), both fed the same Poisson arrival streams. Streams at the offered rates, streams past
+    saturation, and a closed-loop run (every request arrives at t = 0: the loop's capacity).
     Latency runs from each event's scheduled arrival to its results in host memory."""
     pool = gen.generate(cfg, pool_events, with_truth=False)
     rng = np.random.default_rng(seed)
-    out = []
-    for rate in rates:
-        n = int(rate * seconds)
+    served = dict(SERVED, flush_us=flush_us)
+    arms = (("served", served), ("plain_1000", PLAIN_1000))
+    streams = []
+    for rate, secs in [(r, seconds) for r in rates] + [(r, sat_seconds) for r in sat_rates]:
+        n = int(rate * secs)
         arrival = np.cumsum(rng.exponential(1e9 / rate, size=n)).astype(np.int64)
-        row = {"offered_events_per_s": rate, "seconds": seconds, "events": n}
-        row["flush_us"] = flush_us
-        for name, kw in (("served", dict(slots=4, max_batch_events=256, flush_us=flush_us)),
-                         ("plain_1000", dict(slots=1, max_batch_events=1000, flush_us=0.0))):
-            with h.Server(p, max_batch_hits=1 << 22, **kw) as srv:
-                t0 = srv.replay(pool.xy, pool.off, arrival)
-                srv.drain(120)
-                res = srv.poll_numpy(n + 16)
-            lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e3
-            span = (res["t_done_ns"].max() - t0) / 1e9 if len(res) else float("nan")
-            row[name] = {"sustained_events_per_s": len(res) / span, "p50_us": float(np.percentile(lat, 50)),
-                         "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
-                         "completed": int(len(res)), "flags": int(np.bitwise_or.reduce(res["status"]))}
-        out.append(row)
-    return out
+        row = {"offered_events_per_s": rate, "seconds": secs, "events": n, "flush_us": flush_us}
+        for name, kw in arms:
+            row[name] = serve_stream(h, p, kw, pool, arrival)
+        streams.append(row)
+    closed = {}
+    for name, kw in arms:
+        closed[name] = serve_stream(h, p, kw, pool, np.zeros(sat_events, np.int64))
+    # the highest offered rate whose p99 stays within 200 us, per arm
+    best = {}
+    for name, _ in arms:
+        ok = [r["offered_events_per_s"] for r in streams if r[name]["p99_us"] <= 200.0 and
+              r[name]["completed"] == r["events"]]
+        best[name] = max(ok) if ok else None
+    return {"streams": streams, "closed_loop": {"events": sat_events, **closed},
+            "highest_offered_rate_with_p99_le_200us": best,
+            "arms": {"served": served, "plain_1000": PLAIN_1000}}
 
 
 PT_BINS = (50.0, 100.0, 200.0, 400.0, 800.0, 1500.0)
@@ -272,6 +316,56 @@ def track_finding(h, cfg, out, p, first_event: int, n_sample: int, dpt_max=20.0,
             "dphi_rms_mrad": float(1e3 * np.sqrt(np.mean(np.square(dphi)))) if dphi else None}
 
 
+def compare_with_oracle(r, n, ev, out, max_peaks):
+    """Outputs of the timed batch's first n events against the oracle's, element by element:
+    peak counts, kept counts, stored peak records and the kept-hit masks."""
+    npk = out.npeaks[:n].cpu().numpy()
+    nk = out.nkept[:n].cpu().numpy()
+    a = int(ev.off[n])
+    mask = out.mask[:a].cpu().numpy()
+    pk = np.ascontiguousarray(out.peaks[:n].cpu().numpy().astype(np.int16))
+    bad = set(np.nonzero(npk != r.npeaks)[0].tolist()) | set(np.nonzero(nk != r.nkept)[0].tolist())
+    diff = np.nonzero(mask != r.mask)[0]
+    if len(diff):
+        bad |= set((np.searchsorted(ev.off[: n + 1], diff, side="right") - 1).tolist())
+    import oracle
+    view = pk.view(oracle.PEAK_DTYPE).reshape(n, -1)
+    for e in range(n):
+        s = min(int(r.npeaks[e]), max_peaks)
+        if e not in bad and not np.array_equal(view[e, :s], r.peaks[e, :s]):
+            bad.add(e)
+    return {"events": n, "hits": a, "mismatches": len(bad), "compared": "npeaks, nkept, peak records, kept mask",
+            "first_bad_events": sorted(bad)[:5]}
+
+
+def vote_phase_fraction(args, cfg, lane_bank, sms, sm_mhz):
+    """The vote phase alone against the conflict-free atomic ceiling: the phase-timer build of the
+    library (same results, clock64 marks) runs the workload's first 20,000 events in a child
+    process; vote cycles per event on one SM give votes per SM-cycle, against the ceiling per
+    SM-cycle at the clock sampled in the timed region."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--phase-split", "0", "--workload", cfg.name, "--events",
+           str(min(20000, args.events or cfg.n_events))]
+    if getattr(args, "peak_mode", "local-max") == "iterative":
+        cmd += ["--peak-mode", "iterative", "--rel", args.rel, "--nms-radius", str(args.nms_radius)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
+        d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    except (subprocess.SubprocessError, IndexError, ValueError) as e:
+        return {"unavailable": f"phase-timer run failed: {type(e).__name__}"}
+    row = next(iter(d["rows"].values()))
+    if "cycles_per_event" not in row:
+        return {"unavailable": row.get("unavailable", "no phase counters")}
+    cyc = row["cycles_per_event"]
+    votes_per_event = d["hits"] * cfg.n_theta / d["events"]
+    mhz = sm_mhz or 2070.0
+    ceil_per_sm_cycle = lane_bank / (sms * mhz * 1e6)
+    per_cycle = votes_per_event / cyc["vote"]
+    return {"vote_cycles_per_event": cyc["vote"], "event_cycles": sum(cyc.values()), "block": row.get("block"),
+            "votes_per_sm_cycle": per_cycle, "ceiling_per_sm_cycle": ceil_per_sm_cycle,
+            "frac": per_cycle / ceil_per_sm_cycle, "events": d["events"],
+            "basis": "phase-timer build, thread 0 clock64 between the barriers around the vote"}
+
+
 def run_phase_split(args, cfg):
     """Cycles per event of each phase of the fused kernel against CTA size (the paper's
     per-stage study, Sec. 4). The phase-timer build of the library (HOUGH_PHASE_TIMERS, same
@@ -291,7 +385,7 @@ def run_phase_split(args, cfg):
     rows, peak = {}, peak_args(args)
     for blk in (int(x) for x in args.phase_split.split(",")):
         p = None
-        for tiles in (1, 0):  # one tile where the accumulator fits one CTA
+        for tiles in (1, 0):  # one tile where the accumulator fits one CTA (block 0: the plan's)
             q = h.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth, cfg.max_peaks, theta_tiles=tiles,
                          block=blk, events_per_cta=1)
             q.peak_mode, q.rel_num, q.rel_den, q.nms_radius = peak
@@ -322,7 +416,7 @@ def run_phase_split(args, cfg):
         if h.status(out.status, stream) != 0:
             raise RuntimeError("device status flags set")
         r = h.resolve(p)
-        rows[str(blk)] = {"theta_tiles": r.theta_tiles, "events_per_s": n / (e0.elapsed_time(e1) * 1e-3),
+        rows[str(blk)] = {"theta_tiles": r.theta_tiles, "block": r.block, "events_per_s": n / (e0.elapsed_time(e1) * 1e-3),
                           "cycles_per_event": {k: round(v / n) for k, v in cyc.items() if v}}
     print(json.dumps({"metric": "fused-kernel cycles per event by phase (thread 0 of each CTA)",
                       "workload": cfg.name, "events": n, "hits": ev.n_hits, "n_theta": cfg.n_theta,
@@ -421,6 +515,7 @@ def main():
     ap.add_argument("--serve-flush-us", type=float, default=50.0,
                     help="serving loop: longest wait of a request before its partial micro-batch is launched")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-phase", action="store_true", help="skip the vote-phase fraction (phase-timer child run)")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
     ap.add_argument("--shape", default="", help="fixed launch shape 'theta_tiles,block,events_per_cta' (profiling)")
@@ -534,6 +629,12 @@ def main():
     e2e_value = n_events * ws * args.e2e_steps / e2e_s
     h2d = ev.xy.nbytes + ev.off.nbytes
     d2h = runner.d2h_bytes()
+    # one more call, outside the timed region, with CUDA-event marks around every stage
+    h.set_host_timing(True)
+    t1 = time.perf_counter()
+    runner(xy_h, off_h, stream)
+    e2e_stages = dict(runner.stage_ms(), call_wall=1e3 * (time.perf_counter() - t1))
+    h.set_host_timing(False)
 
     if rank != 0:
         if dist is not None:
@@ -543,10 +644,7 @@ def main():
     peaks_meas, peaks_kind = measured_peaks()
     votes = ev.n_hits * cfg.n_theta
     kern = float(np.mean(kern_ms))
-    sm_max = float(peaks_meas.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    alu_peak = sms * 4 * 32 * sm_max * 1e6 / 1e12  # warp-instruction issue: 4 per SM per clock
-    achieved = votes * OPS_PER_VOTE / (kern * 1e-3) / 1e12
     traffic = None
     try:
         with open(PROFILE_TRAFFIC) as f:
@@ -558,16 +656,28 @@ def main():
         traffic = None
     ceiling = probe_atomic_ceiling(h, torch, stream)
     votes_per_s = votes / (kern * 1e-3)
+    npk = out.npeaks.cpu().numpy()
+    stored = int(np.minimum(npk, cfg.max_peaks).sum())
+    # algorithmic HBM bytes of one launch: hits in (8 B) and kept flags out (1 B), per event its
+    # offsets (8 B), peak count and kept count (4 B each), and the stored peak records (8 B each)
+    hbm_bytes = ev.n_hits * 9 + n_events * 16 + stored * PEAK_RECORD_BYTES
+    clk = clocks.summary()
 
-    cpu = None
+    # parity of the timed batch itself: its first --cpu-sample events against the oracle
+    cpu = parity = None
     if not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, _, n, dt = oracle_baseline(cfg, ev, args.cpu_sample, threads, peak_args(args))
+        v, r, n, dt = oracle_baseline(cfg, ev, args.cpu_sample, threads, peak_args(args))
+        parity = compare_with_oracle(r, n, ev, out, cfg.max_peaks)
         v1, _, n1, dt1 = oracle_baseline(cfg, ev, max(1, args.cpu_sample // 10), 1, peak_args(args))
         cpu = {"value": v, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"first {n} events of this batch ({dt:.1f} s wall on {threads} threads, events in parallel)",
                "single_thread": {"value": v1, "unit": "events/s", "cores": 1,
                                  "sample": f"first {n1} events of this batch ({dt1:.1f} s on 1 thread)"}}
+
+    vote_phase = None
+    if not args.no_phase:
+        vote_phase = vote_phase_fraction(args, cfg, ceiling["lane_bank"], sms, clk.get("sm_mhz"))
 
     served = None
     if not args.no_serve:
@@ -578,45 +688,49 @@ def main():
 
     import oracle
     rc, rs = oracle.metrics(out.mask.cpu().numpy(), ev.truth) if ev.truth is not None else (None, None)
+    lane = ceiling["lane_bank"]
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": cfg.name, "events_per_gpu": n_events, "hits_per_gpu": ev.n_hits,
-                   "n_theta": cfg.n_theta, "n_rho": cfg.n_rho, "threshold": cfg.threshold,
-                   "peak_finder": peak_finder_name(args),
-                   "max_peaks": cfg.max_peaks, "launch": {"theta_tiles": plan.theta_tiles, "block": plan.block,
-                                                          "events_per_cta": plan.events_per_cta,
-                                                          "autotuned": not (args.no_tune or args.shape),
-                                                          "tune_best_ms": tune_ms},
+        "config": workload_config(cfg, n_events, args),
+        "launch": {"theta_tiles": plan.theta_tiles, "block": plan.block, "events_per_cta": plan.events_per_cta,
+                   "autotuned": not (args.no_tune or args.shape), "tune_best_ms": tune_ms,
                    "path": "hough_run_batched (persistent kernel + CUDA graph)",
-                   "l2": f"inputs {ev.xy.nbytes / 1e9:.2f} GB > 129 MB L2, no flush",
-                   "parallelism": f"events sharded over {ws} GPU(s)"},
+                   "l2": f"inputs {ev.xy.nbytes / 1e9:.2f} GB > 129 MB L2, no flush", "hits_per_gpu": ev.n_hits},
         "hits_per_s": ev.n_hits * ws * args.steps / (elapsed * 1e-3),
+        "parity": parity,
         "latency": {"batch_ms": ms_step, "note": "every event of the batch completes within one step"},
         "served": served,
-        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "stages_ms": e2e_stages},
         "gpu_launches": 2 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "fused_kernel (persistent)", "achieved": achieved, "peak": alu_peak,
-                     "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": traffic,
-                     "ops_per_vote": OPS_PER_VOTE, "votes_per_launch": votes, "kernel_ms": kern,
-                     "peak_basis": f"{sms} SMs x 4 warp-instructions x 32 lanes per clock at {sm_max:.0f} MHz "
-                                   f"(derived; MEASURED_PEAKS {peaks_kind})",
-                     "votes_per_s": votes_per_s,
-                     "smem_atomic_ceiling": {"lane_bank_ops_per_s": ceiling["lane_bank"],
-                                             "random_word_ops_per_s": ceiling["random_word"],
-                                             "frac_of_lane_bank": votes_per_s / ceiling["lane_bank"],
-                                             "frac_of_random_word": votes_per_s / ceiling["random_word"]},
-                     "hbm_frac": (ev.n_hits * 9 / (kern * 1e-3)) / (peaks_meas["hbm_gbs"] * 1e9)},
-        "clocks": clocks.summary(),
+        "roofline": {"bound": "smem_atomic", "kernel": "fused_kernel (persistent)",
+                     "achieved": votes_per_s / 1e9, "peak": lane / 1e9, "unit": "Gvotes/s",
+                     "frac": votes_per_s / lane, "traffic": traffic,
+                     "peak_basis": "measured red.shared.add.u32 throughput, every lane of a warp on its own bank "
+                                   "(hough_probe_smem_atomics mode 0, 2 CTAs x 1024 threads per SM), timed in this run",
+                     "votes_per_launch": votes, "kernel_ms": kern, "votes_per_s": votes_per_s,
+                     "lane_bank_random_rows_ceiling_votes_per_s": ceiling["lane_bank_random_rows"],
+                     "random_word_ceiling_votes_per_s": ceiling["random_word"],
+                     "frac_of_random_word": votes_per_s / ceiling["random_word"],
+                     "vote_phase": vote_phase,
+                     "hbm": {"algorithmic_bytes": hbm_bytes, "achieved_gbs": hbm_bytes / (kern * 1e-3) / 1e9,
+                             "peak_gbs": peaks_meas["hbm_gbs"], "peak_kind": peaks_kind,
+                             "frac": hbm_bytes / (kern * 1e-3) / (peaks_meas["hbm_gbs"] * 1e9)}},
+        "clocks": clk,
         "status_flags": flags,
-        "physics": {"R_c": rc, "R_s": rs, "mean_peaks_per_event": float(out.npeaks.float().mean().item()),
+        "physics": {"R_c": rc, "R_s": rs, "mean_peaks_per_event": float(npk.mean()),
+                    "note": "at the workload's absolute threshold the filter keeps almost every hit: "
+                            "selection work is sized by the noise peaks",
                     "track_finding": track_finding(h, cfg, out, p, 0, args.physics_events)},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+    if parity is not None and parity["mismatches"]:
+        sys.exit(3)
 
 
 if __name__ == "__main__":

@@ -73,7 +73,10 @@ extern "C" {
 #define HOUGH_F_PEAK_OVERFLOW 4 /* an event had more than max_peaks peaks: the first
                                    max_peaks in raster order are stored and used */
 #define HOUGH_F_EVENT_TOO_LARGE 8
-#define HOUGH_F_TIMEOUT 16
+#define HOUGH_F_TIMEOUT 16       /* serving: the request's micro-batch did not complete within
+                                    HOUGH_SERVE_BATCH_TIMEOUT_NS; its outputs were not written */
+#define HOUGH_F_LAUNCH_FAILED 32 /* serving: the request's micro-batch could not be enqueued (a
+                                    CUDA error); its outputs were not written */
 
 #define HOUGH_STATUS_WORDS 4
 #define HOUGH_MAX_EVENT_HITS 32767
@@ -127,13 +130,16 @@ int hough_map(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t
 int hough_vote(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const int64_t* d_off, int64_t n_events,
                const hough_params* p, int16_t* d_acc, int32_t* d_status, void* stream);
 
-/* Peak finding on d_acc (layout as written by hough_vote): d_npeaks[e] = true peak count,
+/* Peak finding with neighbourhood suppression (Sec. 2, peak finding; the peak_mode field of
+ * hough_params selects the 3x3 local-maximum reading or the paper's iterative finder) on d_acc
+ * (layout as written by hough_vote): d_npeaks[e] = true peak count,
  * d_peaks = [n_events][max_peaks], the first min(count, max_peaks) in raster order; entries past
  * them are left unchanged (this holds for every entry point that writes peaks). */
 int hough_peaks(const int16_t* d_acc, int64_t n_events, const hough_params* p, int32_t* d_npeaks,
                 hough_peak* d_peaks, int32_t* d_status, void* stream);
 
-/* Back-projection selection: d_mask[i] = 1 if hit i is kept, else 0; d_nkept[e] = kept hits of e. */
+/* Back-projection selection (Sec. 2, data filtering: the hits lying on a found peak's curve are
+ * kept): d_mask[i] = 1 if hit i is kept, else 0; d_nkept[e] = kept hits of e. */
 int hough_select(const int64_t* d_uq, const int64_t* d_vq, int64_t n_hits, const int64_t* d_off, int64_t n_events,
                  const hough_params* p, const int32_t* d_npeaks, const hough_peak* d_peaks, uint8_t* d_mask,
                  int32_t* d_nkept, int32_t* d_status, void* stream);
@@ -155,7 +161,9 @@ int hough_circles(const int32_t* d_npeaks, const hough_peak* d_peaks, int64_t n_
  * and batch size (0 is never returned). */
 size_t hough_workspace_size(const hough_params* p, int64_t n_events);
 
-/* Whole path in one pass: map -> rho -> vote -> peaks -> select for every event.
+/* Whole path in one pass: map -> rho -> vote -> peaks -> select for every event (Eq. 1, the
+ * matrix R of Sec. 3, Sec. 2 peak finding and data filtering), one CTA per event or theta tile:
+ * the event-level parallelism of Sec. 3.
  * Outputs as in the stepwise calls; d_checksum (nullable) gets per event
  * sum over cells c = j*n_rho + k of acc[c] * splitmix64_finalizer(c + 1) mod 2^64.
  * d_ws: workspace of ws_bytes >= hough_workspace_size(p, n_events), 256-byte aligned.
@@ -165,7 +173,8 @@ int hough_run(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t
               int32_t* d_npeaks, hough_peak* d_peaks, uint8_t* d_mask, int32_t* d_nkept, uint64_t* d_checksum,
               void* d_ws, size_t ws_bytes, int32_t* d_status, void* stream);
 
-/* Same results as hough_run, scheduled as one persistent launch: CTAs pop
+/* Same results as hough_run, scheduled as one persistent launch over the batch (Sec. 3, events
+ * processed in parallel as a batch; Sec. 4 measures batches of events): CTAs pop
  * (event, tile) work items, largest events first, from a queue in d_ws. The
  * validation/ordering kernel and the persistent kernel are replayed as a CUDA
  * graph cached per (pointers, sizes, parameters, stream). */
@@ -188,6 +197,26 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
 
 /* Device staging bytes hough_run_host needs. */
 size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_events);
+
+/* Stages of hough_run_host, the analogue of the paper's per-stage study (Sec. 4: transfers,
+ * voting, peak finding, result transfer), for hough_host_stage_ms: busy milliseconds of each
+ * stage summed over the call's event chunks (the chunks' stages overlap one another), and the
+ * span from the call's first enqueued work to its last copy. */
+#define HOUGH_HOST_STAGE_H2D 0       /* hits and offsets to the device (and offset rebasing) */
+#define HOUGH_HOST_STAGE_KERNELS 1   /* validation + fused kernel: map, vote, peaks, select */
+#define HOUGH_HOST_STAGE_PACK 2      /* stored peaks packed densely */
+#define HOUGH_HOST_STAGE_D2H 3       /* counts, kept masks and peak offsets to the host */
+#define HOUGH_HOST_STAGE_PEAKS_D2H 4 /* packed peaks to the host */
+#define HOUGH_HOST_STAGE_SPAN 5      /* first work to last copy, on the device clock */
+#define HOUGH_HOST_STAGES 6
+
+/* Measurement hook for the calling host thread: with on != 0, later hough_run_host calls
+ * record CUDA timing events around every stage of every chunk (on the stage's own stream). */
+void hough_set_host_timing(int32_t on);
+
+/* Stage times of this thread's last timed hough_run_host call: min(n, HOUGH_HOST_STAGES)
+ * values in ms into ms. HOUGH_EINVAL if that call was not timed or did not complete. */
+int hough_host_stage_ms(float* ms, int32_t n);
 
 /* Measurement hook for the calling host thread: when both are non-NULL, later fused and
  * batched calls record the CUDA events begin/end (cudaEvent_t passed as void*) on their
@@ -212,9 +241,15 @@ typedef struct hough_serve_config {
   int32_t reserved;
 } hough_serve_config;
 
+/* Longest wait of the serving loop for one micro-batch; past it the batch's requests finish
+ * with HOUGH_F_TIMEOUT and its slot is retired (never reused). */
+#define HOUGH_SERVE_BATCH_TIMEOUT_NS 10000000000LL
+
 /* One finished request. Latency = t_done_ns - t_arrival_ns (steady clock, ns): from the
  * request's arrival (its submit call, or its scheduled time in hough_serve_replay) to the
- * moment its results were in host memory. */
+ * moment its results were in host memory. A request whose status has HOUGH_F_TIMEOUT or
+ * HOUGH_F_LAUNCH_FAILED set has no results: npeaks and nkept are 0 and its output buffers
+ * were not written. */
 typedef struct hough_serve_result {
   int64_t id;
   int32_t status; /* HOUGH_F_* flags raised by the micro-batch the request ran in */
@@ -248,15 +283,60 @@ int hough_serve_poll(void* server, hough_serve_result* out, int32_t max_results,
  * timeout_ns elapsed (HOUGH_ETIMEDOUT). */
 int hough_serve_drain(void* server, int64_t timeout_ns);
 
-/* Replays an arrival schedule from the calling thread: request i is event (i mod pool_events)
- * of the pool (h_off_pool offsets into h_xy_pool) and is submitted at t0 + arrival_ns[i]
- * (busy wait), t0 written to *t_start_ns. A refused admission is retried for up to 10 s with
- * the same scheduled arrival time. Results are not copied out (only counted and timed). */
+/* Replays an arrival schedule from the calling thread: request i (id i) is event
+ * (i mod pool_events) of the pool (h_off_pool offsets into h_xy_pool) and is submitted at
+ * t0 + arrival_ns[i] (busy wait), t0 written to *t_start_ns. A refused admission is retried
+ * for up to 10 s with the same scheduled arrival time. Results are copied out when the
+ * buffers are given (each nullable): request i's kept mask to h_mask_out + m_i, where m_i is
+ * the sum of the hit counts of requests 0 .. i-1, and its stored peaks to
+ * h_peaks_out + i * max_peaks. */
 int hough_serve_replay(void* server, const int32_t* h_xy_pool, const int64_t* h_off_pool, int64_t pool_events,
-                       const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns);
+                       const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns, uint8_t* h_mask_out,
+                       hough_peak* h_peaks_out);
 
 /* Stops the loop, waits for the streams and releases the handle. */
 int hough_serve_close(void* server);
+
+/* Timing record of one micro-batch (steady clock, ns), kept by the serving loop in a ring of
+ * the HOUGH_SERVE_RECORDS most recent batches. */
+typedef struct hough_serve_batch_record {
+  int64_t t_gather;    /* the loop took the batch's requests from the queue */
+  int64_t t_launched;  /* its copies and kernels were enqueued */
+  int64_t t_done_seen; /* the loop saw its completion event */
+  int64_t t_finished;  /* its results were in the callers' buffers and queued */
+  int64_t n_hits;
+  int32_t n_events;
+  int32_t slot;
+} hough_serve_batch_record;
+
+#define HOUGH_SERVE_RECORDS 65536
+
+/* Health of the serving loop and of hough_serve_replay's submitter, for finding stalls: a
+ * pass of the loop (or a submission) that starts more than stall_ns after the previous one is
+ * a stall, recorded with its wall time and the CPU time the thread used meanwhile (near the
+ * wall time: the thread was busy, e.g. in page faults; near zero: it was not running). */
+typedef struct hough_serve_stats {
+  int64_t passes;            /* passes of the serving loop */
+  int64_t batches;           /* micro-batches launched */
+  int64_t stall_ns;          /* threshold (1 ms) */
+  int64_t loop_stalls;       /* gaps between loop passes above stall_ns */
+  int64_t loop_max_gap_ns;   /* the longest gap, */
+  int64_t loop_max_gap_at;   /* when it began (steady clock), */
+  int64_t loop_max_gap_cpu_ns; /* and the loop thread's CPU time during it */
+  int64_t submit_stalls;     /* replay: submissions more than stall_ns behind their schedule */
+  int64_t submit_max_late_ns; /* replay: the latest submission, behind its schedule by this, */
+  int64_t submit_max_late_at; /* at this scheduled time, */
+  int64_t submit_max_late_cpu_ns; /* and the submitting thread's CPU time meanwhile */
+} hough_serve_stats;
+
+/* Copies the loop's statistics into *out, and up to max_records of the most recent batch
+ * records (oldest first) into records (nullable); *n_records (nullable) gets their count. */
+int hough_serve_trace(void* server, hough_serve_stats* out, hough_serve_batch_record* records, int32_t max_records,
+                      int32_t* n_records);
+
+/* Test hook: the next n micro-batch launches of this server fail on the host before anything
+ * is enqueued, as a CUDA launch error would; their requests finish with HOUGH_F_LAUNCH_FAILED. */
+int hough_serve_inject_launch_failures(void* server, int32_t n);
 
 /* Size of the library's built-in scratch array used by hough_run_batched_static. */
 #define HOUGH_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
@@ -272,7 +352,8 @@ int hough_serve_close(void* server);
  * hough_workspace_size(p, n_events), exceeds that size are rejected with HOUGH_EWORKSPACE.
  * The call allocates nothing. The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current), so make that first call before
- * any stream capture. All calls share the one array: calls that can overlap on the GPU (on
+ * any stream capture. That address is kept for the life of the process: after cudaDeviceReset on
+ * a device, do not call this entry point on that device again. All calls share the one array: calls that can overlap on the GPU (on
  * different streams or host threads) race and must be serialised by the caller. Results are
  * identical to hough_run_batched (the same kernels run, launched directly, without a graph). */
 int hough_run_batched_static(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int64_t n_events,
@@ -327,7 +408,8 @@ int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t 
  * each thread issuing `iters` x 16 32-bit shared-memory adds into a `smem_bytes`
  * array with address pattern `mode` (0: each lane its own bank, conflict-free;
  * 1: pseudo-random words; 2: all lanes of a warp on one word; 3: each thread always on
- * the same word of its own bank, so consecutive adds of a thread hit one address).
+ * the same word of its own bank, so consecutive adds of a thread hit one address; 4: each lane
+ * on its own bank at pseudo-random rows, the access pattern of the mirror-pair vote).
  * *d_sink receives a
  * value that keeps the work alive. Time it with events on `stream`. */
 int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,

@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, EPARAM, ESMEM, ECUDA, EWORKSPACE, ETIMEDOUT, EFULL, EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7, -8
-F_BAD_HIT, F_BAD_OFFSETS, F_PEAK_OVERFLOW, F_EVENT_TOO_LARGE, F_TIMEOUT = 1, 2, 4, 8, 16
+F_BAD_HIT, F_BAD_OFFSETS, F_PEAK_OVERFLOW, F_EVENT_TOO_LARGE, F_TIMEOUT, F_LAUNCH_FAILED = 1, 2, 4, 8, 16, 32
 STATUS_WORDS = 4
 MAX_EVENT_HITS = 32767
 HEADER = os.path.join(_build.ROOT, "include", "hough.h")
@@ -48,6 +48,17 @@ class ServeConfig(ctypes.Structure):
     _fields_ = [("params", Params), ("slots", ctypes.c_int32), ("max_batch_events", ctypes.c_int32),
                 ("max_batch_hits", ctypes.c_int64), ("flush_ns", ctypes.c_int64), ("queue_capacity", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "passes", "batches", "stall_ns", "loop_stalls", "loop_max_gap_ns", "loop_max_gap_at", "loop_max_gap_cpu_ns",
+        "submit_stalls", "submit_max_late_ns", "submit_max_late_at", "submit_max_late_cpu_ns")]
+
+
+BATCH_RECORD_DTYPE = [("t_gather", "<i8"), ("t_launched", "<i8"), ("t_done_seen", "<i8"), ("t_finished", "<i8"),
+                      ("n_hits", "<i8"), ("n_events", "<i4"), ("slot", "<i4")]
+SERVE_RECORDS = 65536
 
 
 class ServeResult(ctypes.Structure):
@@ -121,8 +132,10 @@ def load(build: bool = True):
                 "hough_serve_submit": [vp, vp, i64, i64, vp, vp],
                 "hough_serve_poll": [vp, vp, i32, ctypes.POINTER(i32)],
                 "hough_serve_drain": [vp, i64],
-                "hough_serve_replay": [vp, vp, vp, i64, vp, i64, ctypes.POINTER(i64)],
+                "hough_serve_replay": [vp, vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp, vp],
                 "hough_serve_close": [vp],
+                "hough_serve_trace": [vp, ctypes.POINTER(ServeStats), vp, i32, ctypes.POINTER(i32)],
+                "hough_serve_inject_launch_failures": [vp, i32],
             }.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
@@ -133,6 +146,10 @@ def load(build: bool = True):
             lib.hough_host_buffer_size.restype = ctypes.c_size_t
             lib.hough_set_stage_events.argtypes = [vp, vp]
             lib.hough_set_stage_events.restype = None
+            lib.hough_set_host_timing.argtypes = [i32]
+            lib.hough_set_host_timing.restype = None
+            lib.hough_host_stage_ms.argtypes = [vp, i32]
+            lib.hough_host_stage_ms.restype = ctypes.c_int
             lib.hough_strerror.argtypes = [ctypes.c_int]
             lib.hough_strerror.restype = ctypes.c_char_p
             _lib = lib
@@ -364,6 +381,15 @@ class HostRunner:
         self.nkept = torch.zeros(self.n_events, dtype=torch.int32).pin_memory()
         self.cap = cap
 
+    STAGES = ("h2d", "kernels", "pack", "d2h", "peaks_d2h", "span")
+
+    def stage_ms(self):
+        """Per-stage device milliseconds of this thread's last call made with timing on (see
+        set_host_timing): stage busy times summed over the chunks, and the call's span."""
+        buf = (ctypes.c_float * len(self.STAGES))()
+        _check("hough_host_stage_ms", load().hough_host_stage_ms(buf, len(self.STAGES)))
+        return {k: float(buf[i]) for i, k in enumerate(self.STAGES)}
+
     def d2h_bytes(self) -> int:
         """Bytes the last call copied back (results)."""
         return 4 * self.n_events * 2 + 8 * (self.n_events + 1) + self.n_hits + 8 * int(self.peak_off[-1]) + 4
@@ -433,13 +459,32 @@ class Server:
     def drain(self, timeout_s: float = 30.0):
         _check("hough_serve_drain", load().hough_serve_drain(self.handle, int(timeout_s * 1e9)))
 
-    def replay(self, xy_pool, off_pool, arrival_ns) -> int:
-        """Submits request i = pool event i mod n at its scheduled time; returns t0 (ns)."""
+    def replay(self, xy_pool, off_pool, arrival_ns, mask_out=None, peaks_out=None) -> int:
+        """Submits request i = pool event i mod n at its scheduled time; returns t0 (ns). With
+        mask_out (uint8, the requests' hit counts summed) and peaks_out (int16 [requests,
+        max_peaks, 4]) numpy arrays, each request's results are copied there."""
         t0 = ctypes.c_int64()
+        mo = None if mask_out is None else ctypes.c_void_p(mask_out.ctypes.data)
+        po = None if peaks_out is None else ctypes.c_void_p(peaks_out.ctypes.data)
         _check("hough_serve_replay", load().hough_serve_replay(
             self.handle, ctypes.c_void_p(xy_pool.ctypes.data), ctypes.c_void_p(off_pool.ctypes.data),
-            len(off_pool) - 1, ctypes.c_void_p(arrival_ns.ctypes.data), len(arrival_ns), ctypes.byref(t0)))
+            len(off_pool) - 1, ctypes.c_void_p(arrival_ns.ctypes.data), len(arrival_ns), ctypes.byref(t0), mo, po))
         return t0.value
+
+    def trace(self, max_records: int = 65536):
+        """(stats dict, numpy records of the most recent micro-batches, oldest first)."""
+        import numpy as np
+        st = ServeStats()
+        rec = np.zeros(max_records, np.dtype(BATCH_RECORD_DTYPE))
+        n = ctypes.c_int32()
+        _check("hough_serve_trace", load().hough_serve_trace(self.handle, ctypes.byref(st),
+                                                             ctypes.c_void_p(rec.ctypes.data), max_records,
+                                                             ctypes.byref(n)))
+        return {k: int(getattr(st, k)) for k, _ in ServeStats._fields_}, rec[: n.value]
+
+    def inject_launch_failures(self, n: int):
+        """Test hook: the next n micro-batch launches fail on the host before anything is enqueued."""
+        _check("hough_serve_inject_launch_failures", load().hough_serve_inject_launch_failures(self.handle, int(n)))
 
     def close(self):
         if self.handle:
@@ -452,6 +497,11 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def set_host_timing(on: bool):
+    """Per-stage CUDA-event timing of later HostRunner calls on this thread (HostRunner.stage_ms)."""
+    load().hough_set_host_timing(1 if on else 0)
 
 
 def set_stage_events(begin=None, end=None):

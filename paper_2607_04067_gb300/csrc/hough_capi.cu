@@ -60,10 +60,32 @@ WsLayout ws_layout(const Plan& pl, long long n_events) {
   if (T > 1) o = align256(o + 8 * (size_t)(n_events * T));
   w.tile_peaks = o;
   if (T > 1) o = align256(o + sizeof(hough_peak) * (size_t)(n_events * T) * (size_t)pl.max_peaks);
+  const bool it_tiled = T > 1 && pl.peak_mode == HOUGH_PEAK_ITERATIVE;
+  w.n_spill = it_tiled ? (int)std::min<long long>(std::max<long long>(n_events, 1), kSpillSlots) : 0;
+  w.tile_max = o;
+  if (it_tiled) o = align256(o + 4 * (size_t)(n_events * T));
+  w.defer_list = o;
+  if (it_tiled) o = align256(o + 4 * (size_t)(n_events > 0 ? n_events : 1));
+  w.spill = o;
+  if (it_tiled) o = align256(o + 4 * (size_t)w.n_spill * (size_t)pl.n_theta * (size_t)pl.n_rho);
   w.order = o;
   o = align256(o + 4 * (size_t)(n_events > 0 ? n_events : 1));
   w.total = o;
   return w;
+}
+
+void bind_workspace(const Plan& pl, const WsLayout& wl, char* ws, FusedIO& io) {
+  const bool tiled = pl.tiles > 1, it_tiled = tiled && pl.peak_mode == HOUGH_PEAK_ITERATIVE;
+  io.queue = (unsigned long long*)(ws + wl.queue);
+  io.defer_count = (unsigned*)(ws + wl.queue + 8);  // reset with the queue counter by the validation kernel
+  io.tickets = tiled ? (int*)(ws + wl.tickets) : nullptr;
+  io.tile_cnt = tiled ? (int*)(ws + wl.tile_cnt) : nullptr;
+  io.tile_cs = tiled ? (unsigned long long*)(ws + wl.tile_cs) : nullptr;
+  io.tile_peaks = tiled ? (hough_peak*)(ws + wl.tile_peaks) : nullptr;
+  io.tile_max = it_tiled ? (int*)(ws + wl.tile_max) : nullptr;
+  io.defer_list = it_tiled ? (int*)(ws + wl.defer_list) : nullptr;
+  io.spill = it_tiled ? (int*)(ws + wl.spill) : nullptr;
+  io.n_spill = it_tiled ? wl.n_spill : 0;
 }
 
 static constexpr int kSmemBudget = 227 * 1024 - 2048;  // dynamic bytes; static shared memory stays below 2 KB
@@ -88,24 +110,43 @@ static bool layout(Plan& pl) {
   pl.off_idx = o;
   if (pl.mp) o += round16(pl.hit_cap * 2);
   pl.off_pbits = o;  // also the iterative finder's slice and column maxima
+  const bool it_whole = pl.peak_mode == HOUGH_PEAK_ITERATIVE && pl.tiles == 1;
   {
     int iter_words = 0;
-    if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
-      // candidate keys, then 2 state bits a cell (also room for the walk's 1-bit bitmap)
-      const int cand_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 15) / 16;
+    if (it_whole) {
+      // the candidate bitmap, column starts and candidate keys (or the one-pass-per-peak form's
+      // slice maxima)
+      const int cand_words = wpad * pl.nrb + ((pl.n_theta + 4) & ~3) + pl.iter_cap;
       iter_words = iter_scratch_words(pl.n_theta, pl.n_rho, kIterSliceRows);
       if (pl.iter_cap > 0 && cand_words > iter_words) iter_words = cand_words;
     }
     o += round16((wpad * pl.nrb > iter_words ? wpad * pl.nrb : iter_words) * 4);
   }
-  pl.off_cnt = o;  // peak-record keys of the local-maximum scan (the iterative finder has none)
-  if (pl.peak_mode != HOUGH_PEAK_ITERATIVE) o += round16(wpad * pl.key_groups * 4);
+  pl.off_cnt = o;  // record keys of the local-maximum scan or of a tile's candidates
+  if (!it_whole) o += round16(wpad * pl.key_groups * 4);
   pl.off_unres = o;
   o += round16((pl.hit_cap + 1024) / 32 * 4);
   pl.off_trig = o;
   o += round16(2 * pl.n_theta * 2);
   pl.smem_bytes = o;
-  return o <= kSmemBudget;
+  if (o > kSmemBudget) return false;
+  if (pl.peak_mode == HOUGH_PEAK_ITERATIVE && pl.tiles > 1) {
+    // the merging CTA's candidates (a key and a state byte each, after the column starts) in
+    // [off_acc, off_unres); the deferred kernel's finder (scratch, then a bitmap of every cell)
+    // below the trig table
+    const int free_bytes = pl.off_unres - pl.off_acc - 4 * ((pl.n_theta + 4) & ~3);
+    pl.merge_cap = std::min(65535, free_bytes / 5) & ~15;  // candidate indices fit 16 bits
+    const int avail = pl.off_trig / 4, gone = (pl.n_theta * pl.n_rho + 31) / 32;
+    int sh = kIterSliceRows;
+    while (sh < pl.n_rho && iter_scratch_words(pl.n_theta, pl.n_rho, sh) + gone > avail) sh *= 2;
+    const int sw = iter_scratch_words(pl.n_theta, pl.n_rho, sh);
+    if (sw + gone > avail || pl.merge_cap < 64) return false;
+    int cap = 16384;
+    while (cap > 0 && (cap > sw ? cap : sw) + gone > avail) cap = cap > 1024 ? cap / 2 : 0;
+    pl.def_sh = sh;
+    pl.def_cap = cap;
+  }
+  return true;
 }
 
 static int check_params(const hough_params* p) {
@@ -190,10 +231,6 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       sym = tt.c[p->n_theta - 1 - j] == -tt.c[j] && tt.s[p->n_theta - 1 - j] == tt.s[j];
   }
   for (int T = (p->theta_tiles ? p->theta_tiles : 1); T <= (p->theta_tiles ? p->theta_tiles : 64); ++T) {
-    if (p->peak_mode == HOUGH_PEAK_ITERATIVE && T > 1) {
-      if (p->theta_tiles) return HOUGH_EPARAM;  // the iterative finder needs the whole accumulator
-      break;
-    }
     // A mirror-pair tile owns WD = ceil(N/2 / T) words (columns [a, a + WD) and their mirrors;
     // the last tile fewer), in word groups of 32 lanes; other tiles W = ceil(N / T) columns.
     int W;
@@ -274,7 +311,7 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
     // the most staged hits, then (iterative finder) the most candidate keys of its candidate form
     for (int cap = 4096; cap >= 512; cap >>= 1) {
       pl.hit_cap = cap;
-      const int icap0 = pl.peak_mode == HOUGH_PEAK_ITERATIVE ? 8192 : 0;
+      const int icap0 = pl.peak_mode == HOUGH_PEAK_ITERATIVE && T == 1 ? 8192 : 0;
       for (int icap = icap0; icap >= 0; icap = icap > 1024 ? icap / 2 : icap - 1024) {
         pl.iter_cap = icap;
         if (layout(pl)) return HOUGH_OK;
@@ -356,11 +393,7 @@ int prepare_fused(const int32_t* d_xy, int64_t n_hits, const int64_t* d_off, int
   io.nkept = d_nkept;
   io.checksum = (unsigned long long*)d_checksum;
   io.status = d_status;
-  io.queue = (unsigned long long*)(ws + cm.wl.queue);
-  io.tickets = cm.pl.tiles > 1 ? (int*)(ws + cm.wl.tickets) : nullptr;
-  io.tile_cnt = cm.pl.tiles > 1 ? (int*)(ws + cm.wl.tile_cnt) : nullptr;
-  io.tile_cs = cm.pl.tiles > 1 ? (unsigned long long*)(ws + cm.wl.tile_cs) : nullptr;
-  io.tile_peaks = cm.pl.tiles > 1 ? (hough_peak*)(ws + cm.wl.tile_peaks) : nullptr;
+  bind_workspace(cm.pl, cm.wl, ws, io);
   io.n_items = n_events * (long long)cm.pl.tiles;
   return HOUGH_OK;
 }
@@ -758,16 +791,31 @@ size_t hough_host_buffer_size(const hough_params* p, int64_t n_hits, int64_t n_e
   return host_layout(p, n_hits, n_events, L) ? L.total : 256;
 }
 
+// Timing events of one chunk, on the streams of their stages: copy-in [0, 1], kernels [2, 3],
+// packing [3, 4], copy-out of counts, masks and offsets [5, 6], copy-out of the peaks [7, 8].
+constexpr int kStageEvents = 9;
+
 // Streams and events of the pipelined host path, per host thread and device.
 struct HostPipe {
   int device = -1;
   cudaStream_t in = nullptr, out = nullptr, peaks = nullptr;
   cudaEvent_t ev[3 * kHostChunks] = {};
   bool ok = false;
+  bool timing = false;  // per-stage timing of the calls on this thread (hough_set_host_timing)
+  bool tev_ok = false;
+  cudaEvent_t t_start = nullptr;
+  cudaEvent_t tev[kStageEvents * kHostChunks] = {};
+  float stage_ms[HOUGH_HOST_STAGES] = {};
+  bool stage_valid = false;
 };
 
-static HostPipe& host_pipe() {
+static HostPipe& host_pipe_raw() {
   thread_local HostPipe hp;
+  return hp;
+}
+
+static HostPipe& host_pipe() {
+  HostPipe& hp = host_pipe_raw();
   int dev = 0;
   cudaGetDevice(&dev);
   if (!hp.ok || hp.device != dev) {
@@ -777,6 +825,11 @@ static HostPipe& host_pipe() {
     for (int i = 0; i < 3 * kHostChunks && hp.ok; ++i)
       hp.ok = cudaEventCreateWithFlags(&hp.ev[i], cudaEventDisableTiming) == cudaSuccess;
     hp.device = dev;
+    hp.tev_ok = false;
+  }
+  if (hp.ok && hp.timing && !hp.tev_ok) {
+    hp.tev_ok = cudaEventCreate(&hp.t_start) == cudaSuccess;
+    for (int i = 0; i < kStageEvents * kHostChunks && hp.tev_ok; ++i) hp.tev_ok = cudaEventCreate(&hp.tev[i]) == cudaSuccess;
   }
   return hp;
 }
@@ -805,6 +858,11 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
     if (h_off[e + 1] < h_off[e]) return HOUGH_EINVAL;
   HostPipe& hp = host_pipe();
   if (!hp.ok) return cuda_fail(cudaGetLastError());
+  const bool timed = hp.timing && hp.tev_ok;
+  hp.stage_valid = false;
+  auto mark = [&](int c, int k, cudaStream_t s) {
+    return timed ? cudaEventRecord(hp.tev[kStageEvents * c + k], s) : cudaSuccess;
+  };
   char* b = (char*)d_buf;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t mp = (size_t)p->max_peaks;
@@ -823,17 +881,21 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
   const int32_t* d_xy = (const int32_t*)(b + L.xy);
   // the compute stream's earlier work must not see half-written inputs: copy-in starts after it
   e = cudaEventRecord(hp.ev[0], st);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(hp.t_start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.ev[0], 0);
   for (int c = 0; c < K && e == cudaSuccess; ++c) {
     const int64_t e0 = ce[c], n = ce[c + 1] - ce[c], a0 = h_off[e0], nh = h_off[ce[c + 1]] - a0;
     int64_t* roff = d_off + e0 + c;
     cudaEvent_t ev_in = hp.ev[3 * c], ev_comp = hp.ev[3 * c + 1], ev_out = hp.ev[3 * c + 2];
-    e = cudaMemcpyAsync(roff, h_off + e0, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, hp.in);
+    e = mark(c, 0, hp.in);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(roff, h_off + e0, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, hp.in);
     if (e == cudaSuccess && nh)
       e = cudaMemcpyAsync((char*)d_xy + 8 * (size_t)a0, h_xy + 2 * a0, 8 * (size_t)nh, cudaMemcpyHostToDevice, hp.in);
     if (e == cudaSuccess) e = launch_rebase((long long*)roff, n + 1, a0, hp.in);
+    if (e == cudaSuccess) e = mark(c, 1, hp.in);
     if (e == cudaSuccess) e = cudaEventRecord(ev_in, hp.in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in, 0);
+    if (e == cudaSuccess) e = mark(c, 2, st);
     if (e != cudaSuccess) break;
     rc = hough_run_batched(d_xy + 2 * a0, nh, roff, n, p, d_npk + e0, d_pk + e0 * mp, d_mask + a0, d_nk + e0,
                            nullptr, b + L.ws, L.ws_bytes, d_status, stream);
@@ -843,15 +905,20 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
       cudaStreamSynchronize(st);
       return rc;
     }
-    e = launch_pack_peaks(d_npk + e0, d_pk + e0 * mp, n, p->max_peaks, (long long*)(d_poff + e0 + c),
-                          d_dense + e0 * mp, st);
+    e = mark(c, 3, st);
+    if (e == cudaSuccess)
+      e = launch_pack_peaks(d_npk + e0, d_pk + e0 * mp, n, p->max_peaks, (long long*)(d_poff + e0 + c),
+                            d_dense + e0 * mp, st);
+    if (e == cudaSuccess) e = mark(c, 4, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev_comp, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.out, ev_comp, 0);
+    if (e == cudaSuccess) e = mark(c, 5, hp.out);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(h_npeaks + e0, d_npk + e0, 4 * (size_t)n, cudaMemcpyDeviceToHost, hp.out);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(h_nkept + e0, d_nk + e0, 4 * (size_t)n, cudaMemcpyDeviceToHost, hp.out);
     if (e == cudaSuccess && nh) e = cudaMemcpyAsync(h_mask + a0, d_mask + a0, (size_t)nh, cudaMemcpyDeviceToHost, hp.out);
     if (e == cudaSuccess && n)
       e = cudaMemcpyAsync(h_peak_off + e0, d_poff + e0 + c, 8 * (size_t)n, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess) e = mark(c, 6, hp.out);
     if (e == cudaSuccess) e = cudaEventRecord(ev_out, hp.out);
   }
   // stored peaks, chunk by chunk, as each chunk's counts arrive
@@ -868,9 +935,11 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
     }
     if (base + tot > h_peaks_cap) over = true;
     // the chunk's packing finished before its counts were copied, which the host has seen
-    if (!over && tot > 0)
+    e = mark(c, 7, hp.peaks);
+    if (e == cudaSuccess && !over && tot > 0)
       e = cudaMemcpyAsync(h_peaks + base, d_dense + e0 * mp, sizeof(hough_peak) * (size_t)tot,
                           cudaMemcpyDeviceToHost, hp.peaks);
+    if (e == cudaSuccess) e = mark(c, 8, hp.peaks);
     base += tot;
   }
   h_peak_off[n_events] = base;
@@ -881,8 +950,43 @@ int hough_run_host(const int32_t* h_xy, int64_t n_hits, const int64_t* h_off, in
   const cudaError_t s3 = cudaStreamSynchronize(hp.peaks), s4 = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = s1 != cudaSuccess ? s1 : s2 != cudaSuccess ? s2 : s3 != cudaSuccess ? s3 : s4;
   if (e != cudaSuccess) return cuda_fail(e);
+  if (timed) {  // stage busy times summed over the chunks, and the span of the whole call
+    float acc[HOUGH_HOST_STAGES] = {};
+    float last = 0.f;
+    bool ok = true;
+    auto el = [&](cudaEvent_t a, cudaEvent_t z) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) ok = false;
+      return ms;
+    };
+    for (int c = 0; c < K && ok; ++c) {
+      cudaEvent_t* t = hp.tev + kStageEvents * c;
+      acc[HOUGH_HOST_STAGE_H2D] += el(t[0], t[1]);
+      acc[HOUGH_HOST_STAGE_KERNELS] += el(t[2], t[3]);
+      acc[HOUGH_HOST_STAGE_PACK] += el(t[3], t[4]);
+      acc[HOUGH_HOST_STAGE_D2H] += el(t[5], t[6]);
+      acc[HOUGH_HOST_STAGE_PEAKS_D2H] += el(t[7], t[8]);
+      last = std::max(last, std::max(el(hp.t_start, t[6]), el(hp.t_start, t[8])));
+    }
+    acc[HOUGH_HOST_STAGE_SPAN] = last;
+    cudaGetLastError();  // a failed elapsed-time query only invalidates the stage times
+    if (ok) {
+      std::memcpy(hp.stage_ms, acc, sizeof(acc));
+      hp.stage_valid = true;
+    }
+  }
   if (over) return HOUGH_EWORKSPACE;
   return flags ? HOUGH_EDEVICE : HOUGH_OK;
+}
+
+void hough_set_host_timing(int32_t on) { host_pipe_raw().timing = on != 0; }
+
+int hough_host_stage_ms(float* ms, int32_t n) {
+  if (!ms || n < 0) return HOUGH_EINVAL;
+  HostPipe& hp = host_pipe_raw();
+  if (!hp.stage_valid) return HOUGH_EINVAL;
+  for (int i = 0; i < n && i < HOUGH_HOST_STAGES; ++i) ms[i] = hp.stage_ms[i];
+  return HOUGH_OK;
 }
 
 int hough_status(const int32_t* d_status, void* stream, int32_t* host_flags) {
@@ -909,7 +1013,8 @@ const char* hough_strerror(int code) {
     case HOUGH_F_BAD_OFFSETS: return "event offsets invalid";
     case HOUGH_F_PEAK_OVERFLOW: return "more peaks than max_peaks";
     case HOUGH_F_EVENT_TOO_LARGE: return "event has more than HOUGH_MAX_EVENT_HITS hits";
-    case HOUGH_F_TIMEOUT: return "device wait timed out";
+    case HOUGH_F_TIMEOUT: return "micro-batch did not complete in time";
+    case HOUGH_F_LAUNCH_FAILED: return "micro-batch could not be enqueued or failed on the device";
     default: return "unknown code";
   }
 }
@@ -937,7 +1042,7 @@ int hough_selftest_fpbin(int32_t n_theta, int32_t n_rho, uint64_t seed, int64_t 
 
 int hough_probe_smem_atomics(int32_t mode, int32_t ctas_per_sm, int32_t threads, int32_t smem_bytes, int32_t iters,
                              unsigned long long* d_sink, void* stream) {
-  if (!d_sink || mode < 0 || mode > 3 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads % 32) ||
+  if (!d_sink || mode < 0 || mode > 4 || ctas_per_sm < 1 || threads < 32 || threads > 1024 || (threads % 32) ||
       smem_bytes < 4096 || smem_bytes > kSmemBudget || iters < 1)
     return HOUGH_EINVAL;
   cudaError_t e = launch_probe_atomics(mode, ctas_per_sm, threads, smem_bytes, iters, d_sink, (cudaStream_t)stream);

@@ -141,9 +141,10 @@ __host__ __device__ inline int iter_scratch_words(int NT, int NR, int SH) {
 // Iterative peak extraction (the paper's finder, Sec. 2), one pass per peak, over an
 // accumulator behind `cells` (get(j, k) -> votes of a cell not yet suppressed, 0 once
 // suppressed; clear(j, k) suppresses one cell without touching any other cell's value, so that
-// other lanes may read and clear other cells meanwhile; with kPairs true, word(w, k) is the
-// 32-bit word of columns w (low half) and NT - 1 - w (high half) at row k, NT even). The general form of the finder, taken
-// when the sorted form below does not apply.
+// other lanes may read and clear other cells meanwhile; with kPairs true, words() is the count of
+// 32-bit words and word(w, k) the word of column w (low half) and column mirror_col(w) (high
+// half) at row k). The general form of the finder, taken when the sorted form below does not
+// apply.
 // Cells are ordered by the packed word (votes << 16) | (n_rho - 1 - k): within a column the
 // larger word is the cell with more votes and, on equal votes, the smaller k. Across columns
 // the key (votes << 16) | (0xffff - j) orders by votes and, on equal votes, the smaller column
@@ -356,7 +357,7 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
     int m = 0;
     if constexpr (Cells::kPairs) {
       for (int k = warp; k < NR; k += nwarps)
-        for (int w = lane; w < (NT >> 1); w += 32) {
+        for (int w = lane; w < cells.words(); w += 32) {
           const uint32_t x = cells.word(w, k);
           m = max(m, (int)max(x & 0xffffu, x >> 16));
         }
@@ -378,7 +379,7 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
     return ((uint32_t)v << 20) | ((uint32_t)(1023 - j) << 10) | (uint32_t)(1023 - k);
   };
   if constexpr (Cells::kPairs) {
-    const int Wd = NT >> 1;
+    const int Wd = cells.words();
     for (int k = warp; k < NR; k += nwarps) {
       for (int w0 = 0; w0 < Wd; w0 += 32) {
         const int w = w0 + lane;
@@ -393,7 +394,7 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
           const uint32_t lt = (1u << lane) - 1u;
           const int pl = base + __popc(bl & lt), ph = base + __popc(bl) + __popc(bh & lt);
           if (cl && pl < cap) keys[pl] = key_of(vl, w, k);
-          if (ch && ph < cap) keys[ph] = key_of(vh, NT - 1 - w, k);
+          if (ch && ph < cap) keys[ph] = key_of(vh, cells.mirror_col(w), k);
         }
       }
     }

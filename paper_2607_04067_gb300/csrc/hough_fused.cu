@@ -152,11 +152,18 @@ __device__ void stage_vote32(const int2* __restrict__ xy, long long base, int cn
       int slot = 0;
       if (lane == 0) slot = atomicAdd(s_nv, __popc(bal));
       slot = __shfl_sync(kFull, slot, 0);
-      // float form for the float bin path: |u|, |v| <= 44061 are exact in float
+      // float form for the float bin path: |u|, |v| <= 44061 are exact in float; the mirror-pair
+      // layout (idx given) stores hits in pairs (u0, u1, v0, v1) for the vote's f32x2 arithmetic
       if (f) {
         const int at = slot + __popc(bal & lanemask_lt());
-        hb[at] = as_float ? make_int2(__float_as_int((float)u), __float_as_int((float)v)) : make_int2((int)u, (int)v);
-        if (idx) idx[at] = (uint16_t)i;
+        if (idx) {
+          float* fp = reinterpret_cast<float*>(hb) + 4 * (at >> 1) + (at & 1);
+          fp[0] = (float)u;
+          fp[2] = (float)v;
+          idx[at] = (uint16_t)i;
+        } else {
+          hb[at] = as_float ? make_int2(__float_as_int((float)u), __float_as_int((float)v)) : make_int2((int)u, (int)v);
+        }
       }
     }
     if (ok && !f) atomicOr(s_flags, 1);
@@ -392,6 +399,8 @@ struct FusedCells {
   static constexpr bool kPairs = MP;  // word w holds columns w and 2 Wd - 1 - w
   uint32_t* acc;
   int Wd, nrp, rp;  // tile words, padded rows (other layouts), rows with guards (mirror-pair)
+  __device__ int words() const { return Wd; }
+  __device__ int mirror_col(int w) const { return 2 * Wd - 1 - w; }
   __device__ uint32_t word(int w, int k) const { return acc[mp_word(w, k + 1, rp)]; }
   __device__ int get(int j, int k) const {
     if (MP) {
@@ -434,21 +443,69 @@ __device__ __forceinline__ void red_u32(uint32_t addr, uint32_t inc) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
 }
 
+// d = a * b + c on pairs of floats (packed f32x2, each lane rounded as one fused multiply-add).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// Hit i of the mirror-pair staging: pairs of hits (u0, u1, v0, v1).
+__device__ __forceinline__ float2 staged_hit(const float* f, int i) {
+  const float* q = f + 4 * (i >> 1) + (i & 1);
+  return make_float2(q[0], q[2]);
+}
+
+// The four votes of one staged pair of hits (u0, u1, v0, v1) into a word's two columns: row
+// estimates of column j (+A) and of its mirror (-A), packed two hits at a time.
+struct PairEst {
+  float2 k02, k13;  // (hit 0, hit 1) in the low column, then in the high column
+};
+
+__device__ __forceinline__ PairEst pair_est(float4 h, float2 AA, float2 NAA, float2 BB, float2 CC) {
+  const float2 V = fma2(make_float2(h.z, h.w), BB, CC);
+  return PairEst{fma2(make_float2(h.x, h.y), AA, V), fma2(make_float2(h.x, h.y), NAA, V)};
+}
+
+__device__ __forceinline__ bool pair_clear(const PairEst& e, uint32_t am) {
+  return ((__float_as_uint(e.k02.x) & am) != 0u) & ((__float_as_uint(e.k13.x) & am) != 0u) &
+         ((__float_as_uint(e.k02.y) & am) != 0u) & ((__float_as_uint(e.k13.y) & am) != 0u);
+}
+
+__device__ __forceinline__ void pair_red_fast(const PairEst& e, uint32_t base2, int F) {
+  red_u32(base2 + ((__float_as_uint(e.k02.x) >> F) << 7), 1u);
+  red_u32(base2 + ((__float_as_uint(e.k13.x) >> F) << 7), 0x10000u);
+  red_u32(base2 + ((__float_as_uint(e.k02.y) >> F) << 7), 1u);
+  red_u32(base2 + ((__float_as_uint(e.k13.y) >> F) << 7), 0x10000u);
+}
+
+__device__ __forceinline__ void pair_red_exact(const PairEst& e, float4 h, const Plan& pl, uint32_t base,
+                                               uint32_t base2, int cj, int sj) {
+  red_u32(mp_addr(e.k02.x, pl, base, base2, h.x, h.z, cj, sj), 1u);
+  red_u32(mp_addr(e.k13.x, pl, base, base2, h.x, h.z, -cj, sj), 0x10000u);
+  red_u32(mp_addr(e.k02.y, pl, base, base2, h.y, h.w, cj, sj), 1u);
+  red_u32(mp_addr(e.k13.y, pl, base, base2, h.y, h.w, -cj, sj), 0x10000u);
+}
+
 __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, const int2* hb, int nv) {
   const int cj = L.cj, sj = L.sj;
+  const float* hf = reinterpret_cast<const float*>(hb);
   if (L.halo) {
     // A halo word of a tile (columns j and N-1-j), 16 lanes: the same float row estimate as
     // the tile's own words, into a contiguous column (4 bytes per row, guard rows folded
     // like the accumulator's), exact bins when ambiguous.
     if (!L.on) return;
-    const float2* hf = reinterpret_cast<const float2*>(hb);
     const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
     const float c0 = pl.mp_c0;
     const uint32_t am = (uint32_t)pl.mp_amask, base2 = L.col2 - ((uint32_t)pl.mp_k7 >> 5);
     const int F = pl.mp_F;
 #pragma unroll 2
     for (int i = L.p; i < nv; i += L.P) {
-      const float2 h = hf[i];
+      const float2 h = staged_hit(hf, i);
       const float v0 = __fmaf_rn(h.y, B, c0);
       const uint32_t y0 = (uint32_t)__float_as_int(__fmaf_rn(h.x, A, v0));
       const uint32_t y1 = (uint32_t)__float_as_int(__fmaf_rn(-h.x, A, v0));
@@ -465,37 +522,26 @@ __device__ __forceinline__ void vote_mp32(const Plan& pl, const VoteLane& L, con
   }
   const float A = __fmul_rn((float)cj, pl.fp_scale), B = __fmul_rn((float)sj, pl.fp_scale);
   if (!L.on) return;
-  const float c0 = pl.mp_c0;
+  const float2 AA = make_float2(A, A), NAA = make_float2(-A, -A), BB = make_float2(B, B);
+  const float2 CC = make_float2(pl.mp_c0, pl.mp_c0);
   const uint32_t base = L.col1, base2 = L.col1 - (uint32_t)pl.mp_k7;
   const float4* hb4 = reinterpret_cast<const float4*>(hb);
   const int np = nv >> 1, P = L.P;
   const uint32_t am = (uint32_t)pl.mp_amask;
   const int F = pl.mp_F;
+  // One pair of hits (4 votes) a step and one exactness test for the 4: the rare step with an
+  // estimate in the ambiguous window takes the exact path vote by vote. (Two pairs a step with one
+  // test for 8 votes measured slower inside this kernel: 43.4 k against 39.6 k cycles an event.)
 #pragma unroll 4
   for (int q = L.p; q < np; q += P) {
-    const float4 h = hb4[q];
-    const float v0 = __fmaf_rn(h.y, B, c0), v1 = __fmaf_rn(h.w, B, c0);
-    const float k0 = __fmaf_rn(h.x, A, v0), k1 = __fmaf_rn(-h.x, A, v0);
-    const float k2 = __fmaf_rn(h.z, A, v1), k3 = __fmaf_rn(-h.z, A, v1);
-    const uint32_t y0 = (uint32_t)__float_as_int(k0), y1 = (uint32_t)__float_as_int(k1);
-    const uint32_t y2 = (uint32_t)__float_as_int(k2), y3 = (uint32_t)__float_as_int(k3);
-    // one test for the four votes; the rare group with an estimate in the ambiguous
-    // window takes the exact path vote by vote
-    if (((y0 & am) != 0u) & ((y1 & am) != 0u) & ((y2 & am) != 0u) & ((y3 & am) != 0u)) {
-      red_u32(base2 + ((y0 >> F) << 7), 1u);
-      red_u32(base2 + ((y1 >> F) << 7), 0x10000u);
-      red_u32(base2 + ((y2 >> F) << 7), 1u);
-      red_u32(base2 + ((y3 >> F) << 7), 0x10000u);
-    } else {
-      red_u32(mp_addr(k0, pl, base, base2, h.x, h.y, cj, sj), 1u);
-      red_u32(mp_addr(k1, pl, base, base2, h.x, h.y, -cj, sj), 0x10000u);
-      red_u32(mp_addr(k2, pl, base, base2, h.z, h.w, cj, sj), 1u);
-      red_u32(mp_addr(k3, pl, base, base2, h.z, h.w, -cj, sj), 0x10000u);
-    }
+    const float4 g = hb4[q];
+    const PairEst eg = pair_est(g, AA, NAA, BB, CC);
+    if (pair_clear(eg, am)) pair_red_fast(eg, base2, F);
+    else pair_red_exact(eg, g, pl, base, base2, cj, sj);
   }
   if ((nv & 1) && L.p == np % P) {
-    const float2 h = reinterpret_cast<const float2*>(hb)[nv - 1];
-    const float v0 = __fmaf_rn(h.y, B, c0);
+    const float2 h = staged_hit(hf, nv - 1);
+    const float v0 = __fmaf_rn(h.y, B, pl.mp_c0);
     red_u32(mp_addr(__fmaf_rn(h.x, A, v0), pl, base, base2, h.x, h.y, cj, sj), 1u);
     red_u32(mp_addr(__fmaf_rn(-h.x, A, v0), pl, base, base2, h.x, h.y, -cj, sj), 0x10000u);
   }
@@ -948,13 +994,13 @@ __device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx
                              uint32_t* unres) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cap = min(D, kSelCap);
-  const float2* hf = reinterpret_cast<const float2*>(hb);
+  const float* hf = reinterpret_cast<const float*>(hb);
   int kept = 0;
   for (int i0 = 0; i0 < nv; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
     bool hard = false;
     if (i < nv) {
-      const float2 h = hf[i];
+      const float2 h = staged_hit(hf, i);
       bool m = false;
       for (int d = 0; d < cap && !m; ++d) m = sel_test_fp(pl, h.x, h.y, d, fab, cs, bm);
       if (m) {
@@ -980,7 +1026,7 @@ __device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx
         while (bits) {
           const int i = ((wi0 + __ffs(bits) - 1) << 5) + ws;
           bits &= bits - 1u;
-          const float2 h = hf[i];
+          const float2 h = staged_hit(hf, i);
           bool m = false;
           for (int d0 = cap; d0 < D && !m; d0 += 32) {
             const int d = d0 + lane;
@@ -1001,9 +1047,10 @@ __device__ int select_staged(const Plan& pl, const int2* hb, const uint16_t* idx
 struct ItemShared {
   int nv, flags, wide, last, total, D, reuse;
   int kept_tot;
-  long long tstart[64];
+  long long tstart[128];  // segment starts of the tile merge (2 segments a mirror-pair tile)
   int tmp[32];
   unsigned long long red[32];
+  int it_max, it_tq, it_ok, it_C, it_kept;  // iterative finder on theta tiles
 };
 
 // Word W of column P's peak rows dilated by +-hw (hw < 32) and cut to [0, N_rho): bit k is
@@ -1154,25 +1201,403 @@ __device__ int select_event(const Plan& pl, const FusedIO& io, unsigned char* sm
   return kept;
 }
 
+// ---- the iterative finder (Sec. 2) on theta tiles ----
+
+// Maximum (returned to every thread; *s_max must be 0 beforehand) and, with do_cs, this thread's
+// part of the accumulator checksum over the tile's own cells.
 template <bool A32>
-__device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh, long long item,
-                         bool do_cs) {
+__device__ int tile_max_cs(const Plan& pl, const uint32_t* acc, int Wd, int aw, int wt, int j0, bool do_cs,
+                           int* s_max, unsigned long long& cs) {
+  const int NT = pl.n_theta, NR = pl.n_rho, lane = threadIdx.x & 31, warp = threadIdx.x >> 5,
+            nwarps = blockDim.x >> 5;
+  int m = 0;
+  if (pl.mp) {
+    for (int k = warp; k < NR; k += nwarps)
+      for (int w = lane; w < Wd; w += 32) {
+        const uint32_t x = acc[mp_word(w, k + 1, pl.rows_phys)];
+        const unsigned lo = x & 0xffffu, hi = x >> 16;
+        m = max(m, (int)max(lo, hi));
+        if (do_cs) {
+          if (lo) cs += (unsigned long long)lo * mix64((unsigned long long)(aw + w) * NR + k + 1);
+          if (hi) cs += (unsigned long long)hi * mix64((unsigned long long)(NT - 1 - aw - w) * NR + k + 1);
+        }
+      }
+  } else {
+    for (int k = warp; k < NR; k += nwarps)
+      for (int c = lane; c < wt; c += 32) {
+        const int v = acc_get<A32>(acc, c, k, pl.nrho_pad);
+        m = max(m, v);
+        if (do_cs && v) cs += (unsigned long long)v * mix64((unsigned long long)(j0 + c) * NR + k + 1);
+      }
+  }
+  m = __reduce_max_sync(kFull, m);
+  if (lane == 0 && m) atomicMax(s_max, m);
+  __syncthreads();
+  return *s_max;
+}
+
+// Bit k of word (c, k >> 5) of pbits for every tile-local column c whose cell k holds >= tq votes
+// (tile-local columns as in the peak records: mirror-pair word w's low half is column w, its
+// high half column 2 Wd - 1 - w).
+template <bool A32>
+__device__ void tile_candidate_bits(const Plan& pl, const uint32_t* acc, uint32_t* pbits, int Wd, int wt, int tq) {
+  const int NR = pl.n_rho, nrb = pl.nrb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5,
+            nwarps = blockDim.x >> 5;
+  if (pl.mp) {
+    for (int k = warp; k < NR; k += nwarps)
+      for (int w = lane; w < Wd; w += 32) {
+        const uint32_t x = acc[mp_word(w, k + 1, pl.rows_phys)];
+        if ((int)(x & 0xffffu) >= tq) atomicOr(&pbits[w * nrb + (k >> 5)], 1u << (k & 31));
+        if ((int)(x >> 16) >= tq) atomicOr(&pbits[(2 * Wd - 1 - w) * nrb + (k >> 5)], 1u << (k & 31));
+      }
+  } else {
+    for (int k = warp; k < NR; k += nwarps)
+      for (int c = lane; c < wt; c += 32)
+        if (acc_get<A32>(acc, c, k, pl.nrho_pad) >= tq) atomicOr(&pbits[c * nrb + (k >> 5)], 1u << (k & 31));
+  }
+}
+
+__device__ __forceinline__ uint32_t cand_key(int v, int j, int k) {
+  return ((uint32_t)v << 20) | ((uint32_t)(1023 - j) << 10) | (uint32_t)(1023 - k);
+}
+
+// Candidates of the iterative finder in sparse form: keys (cand_key) in raster order, colstart[j]
+// the first candidate of column j and colstart[NT] = C.
+struct SparseCands {
+  uint32_t* keys;
+  const int* colstart;
+  int C;
+};
+
+// Visits every other candidate in the suppression window of candidate i (columns j - R .. j + R
+// and rows k - R .. k + R; a column past either end of the theta range is taken from the other end
+// with the rows mirrored, rows beyond the rho edges do not exist), each column's rows found by a
+// binary search; visit(m, key_m) returns false to stop.
+template <class V>
+__device__ __forceinline__ void visit_window(const SparseCands& s, int NT, int NR, int R, int i, V&& visit) {
+  const uint32_t key = s.keys[i];
+  const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+  for (int d = -R; d <= R; ++d) {
+    int jj = j + d, r0 = max(0, k - R), r1 = min(NR - 1, k + R);
+    if (jj < 0 || jj >= NT) {
+      jj = jj < 0 ? jj + NT : jj - NT;
+      const int q0 = NR - 1 - r1;
+      r1 = NR - 1 - r0;
+      r0 = q0;
+    }
+    int lo = s.colstart[jj];
+    const int end = s.colstart[jj + 1];
+    int hi = end;
+    while (lo < hi) {  // first candidate of column jj at a row >= r0
+      const int mid = (lo + hi) >> 1;
+      if (1023 - (int)(s.keys[mid] & 1023u) < r0) lo = mid + 1;
+      else hi = mid;
+    }
+    for (int m = lo; m < end; ++m) {
+      const uint32_t km = s.keys[m];
+      if (1023 - (int)(km & 1023u) > r1) break;
+      if (m != i && !visit(m, km)) return;
+    }
+  }
+}
+
+// The iterative finder's peaks from its candidates (Sec. 2: the best unsuppressed cell is the next
+// peak and suppresses its window, until the best fails the threshold). The passes keep exactly the
+// candidates that no kept higher-ranked candidate covers, listed by rank; the window relation is
+// symmetric, so a candidate's dominators are the higher-ranked candidates in its own window. They
+// are listed once per candidate (CSR, in work when it fits; else every round rescans the window).
+// Rounds then settle the candidates in parallel: dropped once a dominator is kept, kept once every
+// dominator is dropped; every round settles at least the best undecided one. The kept keys,
+// compacted into the front of keys and ordered by rank (bitonic within keys_room, else by
+// counting), are stored to dst (the first maxp); returns their count. All threads call it.
+__device__ int resolve_sparse(const Plan& pl, const SparseCands& s, int keys_room, unsigned char* work,
+                              int work_bytes, hough_peak* dst, ItemShared& sh) {
+  const int NT = pl.n_theta, NR = pl.n_rho, R = pl.nms_radius, maxp = pl.max_peaks, C = s.C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x, nwarps = bd >> 5;
+  volatile uint8_t* st = work;  // 1 undecided, 2 dropped, 3 kept
+  const int st_bytes = (C + 15) & ~15, doff_words = (C + 4) & ~3;
+  int* doff = reinterpret_cast<int*>(work + st_bytes);
+  uint16_t* dom = reinterpret_cast<uint16_t*>(doff + doff_words);  // candidate indices (C < 65536)
+  const long long dom_cap = ((long long)work_bytes - st_bytes - 4LL * doff_words) / 2;
+  bool csr = dom_cap >= 0;
+  if (csr) {
+    for (int i = tid; i < C; i += bd) {
+      const uint32_t key = s.keys[i];
+      int cnt = 0;
+      visit_window(s, NT, NR, R, i, [&](int, uint32_t km) {
+        cnt += km > key;
+        return true;
+      });
+      doff[i] = cnt;
+    }
+    __syncthreads();
+    const int E = block_exscan(doff, C, sh.tmp);
+    if (tid == 0) doff[C] = E;
+    csr = E <= dom_cap;  // uniform
+    __syncthreads();
+  }
+  if (csr) {
+    for (int i = tid; i < C; i += bd) {
+      const uint32_t key = s.keys[i];
+      int t = doff[i];
+      visit_window(s, NT, NR, R, i, [&](int m, uint32_t km) {
+        if (km > key) dom[t++] = (uint16_t)m;
+        return true;
+      });
+      st[i] = doff[i + 1] == doff[i] ? 3 : 1;  // no dominator: kept at once
+    }
+  } else {
+    for (int i = tid; i < C; i += bd) st[i] = 1;
+  }
+  if (tid < 3) sh.tmp[tid] = 0;
+  __syncthreads();
+  for (int round = 0;; ++round) {
+    int und = 0;
+    for (int i = tid; i < C; i += bd) {
+      if (st[i] != 1) continue;
+      bool drop = false, all = true;
+      if (csr) {
+        for (int t = doff[i], t1 = doff[i + 1]; t < t1; ++t) {
+          const uint8_t sd = st[dom[t]];
+          if (sd == 3) {
+            drop = true;
+            break;
+          }
+          all = all && sd != 1;
+        }
+      } else {
+        const uint32_t key = s.keys[i];
+        visit_window(s, NT, NR, R, i, [&](int m, uint32_t km) {
+          const uint8_t sm = st[m];
+          if (sm == 3) {  // a kept candidate in the window always ranks above this one
+            drop = true;
+            return false;
+          }
+          if (sm == 1 && km > key) all = false;
+          return true;
+        });
+      }
+      if (drop) st[i] = 2;
+      else if (all) st[i] = 3;
+      else ++und;
+    }
+    // undecided count: three rotating counters, so that one barrier a round suffices
+    const int r3 = round % 3;
+    und = __reduce_add_sync(kFull, und);
+    if (lane == 0 && und) atomicAdd(&sh.tmp[r3], und);
+    if (tid == 0) sh.tmp[(r3 + 1) % 3] = 0;
+    __syncthreads();
+    if (sh.tmp[r3] == 0) break;
+  }
+  HOUGH_PHASE(HOUGH_PHASE_IT_RESOLVE);
+  // the kept keys, compacted in place into the front of keys
+  if (tid == 0) sh.it_kept = 0;
+  __syncthreads();
+  for (int i0 = 0; i0 < C; i0 += bd) {
+    const int i = i0 + tid;
+    const bool kept = i < C && st[i] == 3;
+    const uint32_t key = kept ? s.keys[i] : 0u;
+    const unsigned bal = __ballot_sync(kFull, kept);
+    if (lane == 0) sh.tmp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, chunk = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      const int c = sh.tmp[w];
+      before += w < warp ? c : 0;
+      chunk += c;
+    }
+    if (kept) s.keys[sh.it_kept + before + __popc(bal & lanemask_lt())] = key;
+    __syncthreads();
+    if (tid == 0) sh.it_kept += chunk;
+    __syncthreads();
+  }
+  const int nk = sh.it_kept;
+  int N = 32;
+  while (N < nk) N <<= 1;
+  if (nk > 256 && N <= keys_room) {
+    for (int i = nk + tid; i < N; i += bd) s.keys[i] = 0u;
+    __syncthreads();
+    bitonic_desc(s.keys, N);
+    for (int i = tid; i < min(nk, maxp); i += bd) store_peak(dst + i, s.keys[i]);
+  } else {  // rank = the kept keys above it (keys are distinct)
+    for (int i = tid; i < nk; i += bd) {
+      const uint32_t key = s.keys[i];
+      int r = 0;
+      for (int m = 0; m < nk; ++m) r += s.keys[m] > key;
+      if (r < maxp) store_peak(dst + r, key);
+    }
+  }
+  __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_ORDER);
+  return nk;
+}
+
+// The iterative finder on a whole accumulator in the CTA (one tile). The maximum gives the
+// threshold tq = max(T, ceil(rel max)); the cells >= tq are marked in a bitmap (pbits) and
+// listed in raster order, a thread per column, with their column starts; the accumulator's
+// shared memory is then the work area of the resolution. Events whose maximum exceeds the keys'
+// 12-bit vote field, or with more candidates than the plan's iter_cap, take the one-pass-per-peak
+// form on the accumulator instead. Records in extraction order; returns the count.
+template <bool A32, class Cells>
+__device__ int iterative_whole(const Plan& pl, Cells& cells, unsigned char* smem, ItemShared& sh, hough_peak* dst) {
+  const int NT = pl.n_theta, NR = pl.n_rho, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5,
+            nwarps = blockDim.x >> 5, bd = blockDim.x;
+  uint32_t* acc = reinterpret_cast<uint32_t*>(smem + pl.off_acc);
+  uint32_t* pbits = reinterpret_cast<uint32_t*>(smem + pl.off_pbits);
+  const int bm_words = pl.groups * 32 * pl.nrb;
+  int* colstart = reinterpret_cast<int*>(pbits + bm_words);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(colstart + ((NT + 4) & ~3));
+  if (tid == 0) sh.it_max = 0;
+  __syncthreads();
+  {  // the maximum (a warp takes rows, its lanes words of two columns, or columns)
+    int m = 0;
+    if constexpr (Cells::kPairs) {
+      for (int k = warp; k < NR; k += nwarps)
+        for (int w = lane; w < cells.words(); w += 32) {
+          const uint32_t x = cells.word(w, k);
+          m = max(m, (int)max(x & 0xffffu, x >> 16));
+        }
+    } else {
+      for (int k = warp; k < NR; k += nwarps)
+        for (int j = lane; j < NT; j += 32) m = max(m, cells.get(j, k));
+    }
+    m = __reduce_max_sync(kFull, m);
+    if (lane == 0 && m) atomicMax(&sh.it_max, m);
+  }
+  __syncthreads();
+  HOUGH_PHASE(HOUGH_PHASE_IT_MAX);
+  const int amax = sh.it_max;
+  const long long need = ((long long)pl.rel_num * amax + pl.rel_den - 1) / pl.rel_den;
+  const int tq = (int)max((long long)pl.threshold, need);
+  int C = -1;
+  if (amax <= 4095 && pl.iter_cap > 0) {
+    tile_candidate_bits<A32>(pl, acc, pbits, pl.mp ? NT >> 1 : 0, NT, tq);
+    __syncthreads();
+    for (int j = tid; j < NT; j += bd) {
+      int c = 0;
+      for (int w = 0; w < pl.nrb; ++w) c += __popc(pbits[j * pl.nrb + w]);
+      colstart[j] = c;
+    }
+    colstart[NT] = 0;
+    __syncthreads();
+    C = block_exscan(colstart, NT + 1, sh.tmp);
+    if (C <= pl.iter_cap) {
+      for (int j = tid; j < NT; j += bd) {
+        int pos = colstart[j];
+        for (int w = 0; w < pl.nrb; ++w) {
+          uint32_t bits = pbits[j * pl.nrb + w];
+          while (bits) {
+            const int k = (w << 5) + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            keys[pos++] = cand_key(cells.get(j, k), j, k);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  HOUGH_PHASE(HOUGH_PHASE_IT_COLLECT);
+  if (C < 0 || C > pl.iter_cap)  // uniform
+    return extract_iterative_passes(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den,
+                                    pl.nms_radius, pl.max_peaks, pbits, dst, sh.tmp);
+  const SparseCands sc{keys, colstart, C};
+  return resolve_sparse(pl, sc, pl.iter_cap, reinterpret_cast<unsigned char*>(acc), pl.region_bytes, dst, sh);
+}
+
+// The event's peaks from its tiles' candidate lists, in the last tile CTA of the event. The
+// event's threshold tq = max(T, ceil(rel max)) comes from the tiles' maxima. The candidates (cells
+// >= tq) are gathered in raster order, with the first candidate of every column (colstart), into
+// the CTA's free shared memory, and settled in rounds as in the untiled finder (a candidate is
+// dropped once a kept candidate lies in its window, kept once every higher-ranked candidate in
+// its window is dropped), each window looked up column by column by binary search over rows.
+// The kept ones, sorted by rank, are the peaks in extraction order. Returns their count, or -1
+// (nothing written) when a tile could not publish all its candidates or they exceed the room.
+__device__ int merge_iterative(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh, long long e) {
+  const int T = pl.tiles, NT = pl.n_theta, NR = pl.n_rho, R = pl.nms_radius, maxp = pl.max_peaks;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x, nwarps = bd >> 5;
+  const int nseg = pl.mp ? 2 * T : T, cap = pl.merge_cap;
+  int* colstart = reinterpret_cast<int*>(smem + pl.off_acc);  // NT + 1
+  uint32_t* keys = reinterpret_cast<uint32_t*>(colstart + ((NT + 4) & ~3));
+  if (tid == 0) {
+    int M = 0;
+    bool ok = true;
+    long long run = 0;
+    for (int tt = 0; tt < T; ++tt) {
+      M = max(M, __ldcg(io.tile_max + e * T + tt));
+      ok = ok && __ldcg(io.tile_cnt + 2 * (e * T + tt)) <= maxp;
+    }
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int tt = sg < T ? sg : 2 * T - 1 - sg;
+      const int all = __ldcg(io.tile_cnt + 2 * (e * T + tt)), lo = __ldcg(io.tile_cnt + 2 * (e * T + tt) + 1);
+      sh.tstart[sg] = run;
+      run += sg < T ? lo : all - lo;
+    }
+    const long long need = ((long long)pl.rel_num * M + pl.rel_den - 1) / pl.rel_den;
+    sh.it_tq = (int)max((long long)pl.threshold, need);
+    sh.it_ok = ok && M <= 4095 ? 1 : 0;  // a key holds votes in 12 bits
+    sh.it_C = 0;
+  }
+  __syncthreads();
+  if (!sh.it_ok) return -1;  // uniform
+  const int tq = sh.it_tq;
+  // gather the candidates >= tq, in order
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int tt = sg < T ? sg : 2 * T - 1 - sg;
+    const int all = __ldcg(io.tile_cnt + 2 * (e * T + tt)), lo = __ldcg(io.tile_cnt + 2 * (e * T + tt) + 1);
+    const int from = sg < T ? 0 : lo, ct = sg < T ? lo : all - lo;
+    const hough_peak* src = io.tile_peaks + (e * T + tt) * (long long)maxp + from;
+    for (int i0 = 0; i0 < ct; i0 += bd) {
+      const int i = i0 + tid;
+      uint32_t key = 0;
+      bool keep = false;
+      if (i < ct) {
+        const int2 r = __ldcg(reinterpret_cast<const int2*>(src) + i);
+        const int j = r.x & 0xffff, k = (r.x >> 16) & 0xffff, v = r.y & 0xffff;
+        keep = v >= tq;
+        key = cand_key(v, j, k);
+      }
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (lane == 0) sh.tmp[warp] = __popc(bal);
+      __syncthreads();
+      int before = 0, chunk = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        const int c = sh.tmp[w];
+        before += w < warp ? c : 0;
+        chunk += c;
+      }
+      const int pos = sh.it_C + before + __popc(bal & lanemask_lt());
+      if (keep && pos < cap) keys[pos] = key;
+      __syncthreads();
+      if (tid == 0) sh.it_C += chunk;
+      __syncthreads();
+    }
+  }
+  const int C = sh.it_C;
+  if (C > cap) return -1;  // uniform
+  // first candidate of every column (keys are in raster order)
+  for (int j = tid; j <= NT; j += bd) colstart[j] = 0;
+  __syncthreads();
+  for (int i = tid; i < C; i += bd) atomicAdd(&colstart[1023 - (int)((keys[i] >> 10) & 1023u)], 1);
+  __syncthreads();
+  block_exscan(colstart, NT + 1, sh.tmp);
+  const SparseCands sc{keys, colstart, C};
+  unsigned char* work = reinterpret_cast<unsigned char*>(keys + C);
+  return resolve_sparse(pl, sc, cap, work, (int)(smem + pl.off_unres - work), io.peaks + e * (long long)maxp, sh);
+}
+
+// Steps 1-2 of a work item: clears the CTA's accumulator of theta tile t (with the halo columns,
+// the peak bitmap and the flags) and votes the event's hits [a, a + n) into it, chunk by chunk.
+template <bool A32>
+__device__ void vote_tile(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh, long long a, int n,
+                          int t) {
   uint32_t* acc = reinterpret_cast<uint32_t*>(smem + pl.off_acc);
   uint32_t* halo = reinterpret_cast<uint32_t*>(smem + pl.off_halo);
   int2* hb = reinterpret_cast<int2*>(smem + pl.off_hits);
   longlong2* hw = reinterpret_cast<longlong2*>(smem + pl.off_hits);
   uint32_t* pbits = reinterpret_cast<uint32_t*>(smem + pl.off_pbits);
-  int* cnt = reinterpret_cast<int*>(smem + pl.off_cnt);
   const int16_t* tc = reinterpret_cast<const int16_t*>(smem + pl.off_trig);
   const int16_t* ts = tc + pl.n_theta;
-
-  const int T = pl.tiles, NT = pl.n_theta, NR = pl.n_rho, nrp = pl.nrho_pad;
-  const long long e = io.order ? (long long)io.order[item / T] : item / T;
-  const int t = (int)(item % T);
-  const long long a = io.off[e];
-  const long long nll = io.off[e + 1] - a;
-  const bool too_large = nll > HOUGH_MAX_EVENT_HITS;
-  const int n = too_large ? 0 : (int)nll;
+  const int T = pl.tiles, NT = pl.n_theta, nrp = pl.nrho_pad;
   const int j0 = t * pl.tile_w;
   const int wt = min(pl.tile_w, NT - j0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x;
@@ -1190,11 +1615,12 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   L.cj = L.sj = 0;
   L.col1 = L.col2 = 0;
   const uint32_t acc_s = (uint32_t)__cvta_generic_to_shared(acc);
+  const bool want_halo = pl.peak_mode != HOUGH_PEAK_ITERATIVE;  // only the 3x3 test reads the halo
   if (L.halo && pl.mp) {
     // lanes 0-15: word aw - 1, lanes 16-31: word aw + Wd (both of its columns), each lane
     // a sixteenth of the hits; none at the theta wrap or at the middle word
     const int hs = lane >> 4, wg = hs ? aw + Wd : aw - 1;
-    L.on = hs ? (aw + Wd < (NT >> 1)) : (aw > 0);
+    L.on = want_halo && (hs ? (aw + Wd < (NT >> 1)) : (aw > 0));
     if (L.on) {
       L.cj = tc[wg];
       L.sj = ts[wg];
@@ -1204,7 +1630,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     L.P = 16;
   } else if (L.halo) {
     const int jh = lane < 16 ? (j0 - 1 + NT) % NT : (j0 + wt) % NT;
-    L.on = true;
+    L.on = want_halo;
     L.cj = tc[jh];
     L.sj = ts[jh];
     L.col2 = (uint32_t)__cvta_generic_to_shared(halo) + (uint32_t)((lane >> 4) * (nrp >> 1)) * 4u;
@@ -1250,7 +1676,10 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     if (T > 1)
       for (int i = tid; i < (pl.mp ? 2 * pl.rows_phys : nrp); i += bd) halo[i] = 0u;
     for (int i = tid; i < wpad * pl.nrb; i += bd) pbits[i] = 0;
-    if (tid == 0) sh.flags = 0;
+    if (tid == 0) {
+      sh.flags = 0;
+      sh.it_max = 0;
+    }
   }
 
   // 2. map + vote, chunk by chunk
@@ -1298,12 +1727,39 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
   __syncthreads();
   HOUGH_PHASE(n > 0 ? HOUGH_PHASE_VOTE : HOUGH_PHASE_CLEAR);
 
+}
+
+template <bool A32>
+__device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem, ItemShared& sh, long long item,
+                         bool do_cs) {
+  uint32_t* acc = reinterpret_cast<uint32_t*>(smem + pl.off_acc);
+  uint32_t* halo = reinterpret_cast<uint32_t*>(smem + pl.off_halo);
+  uint32_t* pbits = reinterpret_cast<uint32_t*>(smem + pl.off_pbits);
+  int* cnt = reinterpret_cast<int*>(smem + pl.off_cnt);
+  const int16_t* tc = reinterpret_cast<const int16_t*>(smem + pl.off_trig);
+  const int16_t* ts = tc + pl.n_theta;
+
+  const int T = pl.tiles, NT = pl.n_theta, NR = pl.n_rho, nrp = pl.nrho_pad;
+  const long long e = io.order ? (long long)io.order[item / T] : item / T;
+  const int t = (int)(item % T);
+  const long long a = io.off[e];
+  const long long nll = io.off[e + 1] - a;
+  const bool too_large = nll > HOUGH_MAX_EVENT_HITS;
+  const int n = too_large ? 0 : (int)nll;
+  const int j0 = t * pl.tile_w;
+  const int wt = min(pl.tile_w, NT - j0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, bd = blockDim.x;
+  const int Wd = pl.mp ? (wt >> 1) : 0, aw = t * (pl.tile_w >> 1);
+
+  vote_tile<A32>(pl, io, smem, sh, a, n, t);
+
   // 3-4. peaks
   const int maxp = pl.max_peaks;
   int total = 0, n_low = 0;
   unsigned long long cs_tile = 0;
-  if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
-    // the paper's iterative finder (one tile, by the plan): the checksum first, then the
+  int tmax = 0;
+  if (pl.peak_mode == HOUGH_PEAK_ITERATIVE && T == 1) {
+    // the paper's iterative finder on a whole accumulator: the checksum first, then the
     // extraction, which clears the cells it suppresses; records in extraction order
     if (pl.mp) {
       mp_fold(pl, acc, Wd, nullptr);
@@ -1321,18 +1777,27 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       }
       __syncthreads();
       HOUGH_PHASE(HOUGH_PHASE_SCAN);
-      return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
-                               maxp, pbits, pl.iter_cap, nullptr, (NT * NR + 15) >> 4,
-                               io.peaks + e * (long long)maxp, sh.tmp);
+      return iterative_whole<A32>(pl, cells, smem, sh, io.peaks + e * (long long)maxp);
     };
     total = pl.mp ? iterative(FusedCells<A32, true>{acc, Wd, nrp, pl.rows_phys})
                   : iterative(FusedCells<A32, false>{acc, Wd, nrp, pl.rows_phys});
     n_low = total;
   } else {
-    // 3. peak scan
+    // 3. peak scan, or (the iterative finder on theta tiles) the tile's candidates: every cell
+    // at or above the tile's own relative threshold, a superset of the cells the event's
+    // threshold admits (the event's maximum is at least the tile's)
     unsigned long long csum = 0;
     const bool packed = !pl.mp && !A32 && (NR & 1) == 0;
-    if (pl.mp) {
+    if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
+      if (pl.mp) {
+        mp_fold(pl, acc, Wd, nullptr);
+        __syncthreads();
+        HOUGH_PHASE(HOUGH_PHASE_FOLD);
+      }
+      tmax = tile_max_cs<A32>(pl, acc, Wd, aw, wt, j0, do_cs, &sh.it_max, csum);
+      const long long need = ((long long)pl.rel_num * tmax + pl.rel_den - 1) / pl.rel_den;
+      tile_candidate_bits<A32>(pl, acc, pbits, Wd, wt, (int)max((long long)pl.threshold, need));
+    } else if (pl.mp) {
       mp_fold(pl, acc, Wd, T > 1 ? halo : nullptr);
       __syncthreads();
       HOUGH_PHASE(HOUGH_PHASE_FOLD);
@@ -1430,6 +1895,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       io.tile_cnt[2 * (e * T + t)] = total;
       io.tile_cnt[2 * (e * T + t) + 1] = n_low;
       if (do_cs) io.tile_cs[e * T + t] = cs_tile;
+      if (io.tile_max) io.tile_max[e * T + t] = tmax;
     }
     __threadfence();
     __syncthreads();
@@ -1444,6 +1910,25 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
     // tiles) their high segments in reverse tile order. Segment s < T is tile s's records
     // [0, lo); segment T + i is tile T-1-i's records [lo, all).
     const int nseg = pl.mp ? 2 * T : T;
+    if (pl.peak_mode == HOUGH_PEAK_ITERATIVE) {
+      ev_total = merge_iterative(pl, io, smem, sh, e);
+      if (tid == 0) {
+        unsigned long long csa = 0;
+        if (do_cs)
+          for (int tt = 0; tt < T; ++tt) csa += __ldcg(io.tile_cs + e * T + tt);
+        sh.red[0] = csa;
+      }
+      __syncthreads();
+      ev_cs = sh.red[0];
+      if (ev_total < 0) {  // deferred: the fallback kernel writes this event's outputs
+        if (tid == 0) {
+          if (io.checksum) io.checksum[e] = ev_cs;
+          io.defer_list[atomicAdd(io.defer_count, 1u)] = (int)e;
+          if (sh.flags) atomicOr(io.status, sh.flags);
+        }
+        return;
+      }
+    } else {
     if (tid == 0) {
       long long run = 0;
       unsigned long long csa = 0;
@@ -1474,6 +1959,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       }
     }
     __syncthreads();
+    }
   }
 
   // 6. event outputs and selection (single tile, or the last tile)
@@ -1533,6 +2019,103 @@ __global__ void __launch_bounds__(1024) fused_kernel(const Plan pl, const FusedI
   }
 }
 
+// Accumulator of one deferred event in HBM (int32 cells, raster order) for the iterative finder;
+// suppressed cells are kept in a shared bitmap.
+struct SpillCells {
+  static constexpr bool kPairs = false;
+  const int* A;
+  uint32_t* gone;
+  int NR;
+  __device__ int get(int j, int k) const {
+    const int c = j * NR + k;
+    return ((gone[c >> 5] >> (c & 31)) & 1u) ? 0 : A[c];
+  }
+  __device__ void clear(int j, int k) {
+    const int c = j * NR + k;
+    atomicOr(&gone[c >> 5], 1u << (c & 31));
+  }
+};
+
+// Events the tiled iterative finder deferred (a tile's candidates beyond its record slots, more
+// candidates than the merging CTA holds, or a maximum beyond the keys' 12-bit vote field): one
+// CTA per HBM accumulator slot takes them in turn, votes every tile of the event in shared
+// memory exactly as the fused kernel does and stores the cells to its slot, runs the iterative
+// finder there (the stepwise form, any size) and selects the hits. Count and list were written
+// by the fused kernel before this launch on the same stream.
+template <bool A32>
+__global__ void __launch_bounds__(1024) deferred_kernel(const Plan pl, const FusedIO io, const TrigTable trig) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ItemShared sh;
+  if (io.status[1] != 0) return;
+  const unsigned cnt = *io.defer_count;
+  if (blockIdx.x >= cnt) return;
+  int16_t* tc = reinterpret_cast<int16_t*>(smem + pl.off_trig);
+  for (int j = threadIdx.x; j < pl.n_theta; j += blockDim.x) {
+    tc[j] = trig.c[j];
+    tc[pl.n_theta + j] = trig.s[j];
+  }
+  __syncthreads();
+  const int T = pl.tiles, NT = pl.n_theta, NR = pl.n_rho, tid = threadIdx.x, bd = blockDim.x, lane = tid & 31;
+  const uint32_t* acc = reinterpret_cast<const uint32_t*>(smem + pl.off_acc);
+  int* A = io.spill + (long long)blockIdx.x * NT * NR;
+  for (unsigned d = blockIdx.x; d < cnt; d += gridDim.x) {
+    const long long e = io.defer_list[d];
+    const long long a = io.off[e], nll = io.off[e + 1] - a;
+    const int n = nll > HOUGH_MAX_EVENT_HITS ? 0 : (int)nll;  // a too-large event is never deferred
+    int flags = 0;
+    for (int t = 0; t < T; ++t) {
+      vote_tile<A32>(pl, io, smem, sh, a, n, t);
+      const int j0 = t * pl.tile_w, wt = min(pl.tile_w, NT - j0), Wd = pl.mp ? (wt >> 1) : 0,
+                aw = t * (pl.tile_w >> 1);
+      if (pl.mp) {
+        mp_fold(pl, const_cast<uint32_t*>(acc), Wd, nullptr);
+        __syncthreads();
+        for (int i = tid; i < Wd * NR; i += bd) {
+          const int w = i / NR, k = i - w * NR;
+          const uint32_t x = acc[mp_word(w, k + 1, pl.rows_phys)];
+          A[(aw + w) * NR + k] = (int)(x & 0xffffu);
+          A[(NT - 1 - aw - w) * NR + k] = (int)(x >> 16);
+        }
+      } else {
+        for (int i = tid; i < wt * NR; i += bd) {
+          const int c = i / NR, k = i - c * NR;
+          A[(j0 + c) * NR + k] = acc_get<A32>(acc, c, k, pl.nrho_pad);
+        }
+      }
+      flags |= sh.flags;
+      __syncthreads();
+    }
+    __threadfence_block();
+    // the finder: its scratch first, then the suppression bitmap, below the trig table
+    uint32_t* scratch = reinterpret_cast<uint32_t*>(smem);
+    const int sw = iter_scratch_words(NT, NR, pl.def_sh);
+    uint32_t* gone = scratch + (sw > pl.def_cap ? sw : pl.def_cap);
+    for (int i = tid; i < (NT * NR + 31) >> 5; i += bd) gone[i] = 0u;
+    __syncthreads();
+    SpillCells cells{A, gone, NR};
+    hough_peak* dst = io.peaks + e * (long long)pl.max_peaks;
+    const int total = extract_iterative(cells, NT, NR, pl.def_sh, pl.threshold, pl.rel_num, pl.rel_den,
+                                        pl.nms_radius, pl.max_peaks, scratch, pl.def_cap, gone, 0, dst, sh.tmp);
+    if (tid == 0) {
+      io.npeaks[e] = total;
+      if (total > pl.max_peaks) flags |= HOUGH_F_PEAK_OVERFLOW;
+      sh.reuse = 0;  // the staged hits were overwritten by the finder
+    }
+    __syncthreads();
+    int kept = select_event(pl, io, smem, sh, tc, tc + NT, a, n, dst, min(total, pl.max_peaks), false);
+    if (tid == 0) sh.kept_tot = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(kFull, kept, o);
+    if (lane == 0 && kept) atomicAdd(&sh.kept_tot, kept);
+    __syncthreads();
+    if (tid == 0) {
+      io.nkept[e] = sh.kept_tot;
+      if (flags) atomicOr(io.status, flags);
+    }
+    __syncthreads();
+  }
+}
+
 // Validates offsets (sets status word 1 for the following kernels), resets the persistent
 // queue and the per-event tickets, and orders events by decreasing hit count.
 __global__ void __launch_bounds__(1024) prep_kernel(const long long* off, long long ne, long long nh, int* status,
@@ -1549,7 +2132,10 @@ __global__ void __launch_bounds__(1024) prep_kernel(const long long* off, long l
   if (threadIdx.x == 0) {
     status[1] = bad;
     if (bad) atomicOr(status, HOUGH_F_BAD_OFFSETS);
-    if (queue) *queue = 0ull;
+    if (queue) {
+      queue[0] = 0ull;  // the persistent queue's item counter
+      queue[1] = 0ull;  // the count of deferred events (tiled iterative finder)
+    }
   }
   if (bad) return;
   if (tickets)
@@ -1664,14 +2250,19 @@ int fused_max_ctas_per_sm(const Plan& pl) {
 
 cudaError_t launch_fused(const Plan& pl, const FusedIO& io, const TrigTable& trig, int grid, cudaStream_t st) {
   cudaError_t err;
+  const bool deferred = pl.peak_mode == HOUGH_PEAK_ITERATIVE && pl.tiles > 1;
   if (pl.acc32) {
     err = set_smem((const void*)fused_kernel<true>, pl.smem_bytes);
+    if (err == cudaSuccess && deferred) err = set_smem((const void*)deferred_kernel<true>, pl.smem_bytes);
     if (err != cudaSuccess) return err;
     fused_kernel<true><<<grid, pl.threads, pl.smem_bytes, st>>>(pl, io, trig);
+    if (deferred) deferred_kernel<true><<<io.n_spill, pl.threads, pl.smem_bytes, st>>>(pl, io, trig);
   } else {
     err = set_smem((const void*)fused_kernel<false>, pl.smem_bytes);
+    if (err == cudaSuccess && deferred) err = set_smem((const void*)deferred_kernel<false>, pl.smem_bytes);
     if (err != cudaSuccess) return err;
     fused_kernel<false><<<grid, pl.threads, pl.smem_bytes, st>>>(pl, io, trig);
+    if (deferred) deferred_kernel<false><<<io.n_spill, pl.threads, pl.smem_bytes, st>>>(pl, io, trig);
   }
   return cudaGetLastError();
 }

@@ -43,6 +43,9 @@ struct Plan {
   float mp_c0;    // N_rho/2 + 1 + 2^b + W/2 2^-F
   long long mp_lsq;  // fast path when u^2 + v^2 <= mp_lsq (rho within half a bin of the range)
   float fp_scale, fp_c0, fp_khi, fp_dlo, fp_dhi;  // N_rho/2H, N_rho/2, N_rho-1/2, delta-1/2, -delta-1/2
+  // iterative finder on theta tiles: candidate keys the merging CTA holds; slice height and
+  // candidate keys of the deferred kernel's finder
+  int merge_cap, def_sh, def_cap;
   // shared-memory layout in bytes
   int off_acc, region_bytes, off_halo, off_hits, off_idx, off_pbits, off_cnt, off_unres, off_trig, smem_bytes;
   BinMagic magic;
@@ -65,16 +68,29 @@ struct FusedIO {
   int* tile_cnt;                 // [n_events * tiles]
   unsigned long long* tile_cs;   // [n_events * tiles]
   hough_peak* tile_peaks;        // [n_events * tiles * max_peaks]
+  // iterative finder on theta tiles: each tile's maximum, the events deferred to the fallback
+  // kernel (count, list) and its accumulators in HBM (n_spill of n_theta * n_rho int32 cells)
+  int* tile_max;                 // [n_events * tiles]
+  unsigned* defer_count;
+  int* defer_list;               // [n_events]
+  int* spill;
+  int n_spill;
   long long n_items;
   int persistent;
 };
 
 // Workspace carve-up (byte offsets inside the caller's buffer).
 struct WsLayout {
-  size_t queue, tickets, tile_cnt, tile_cs, tile_peaks, order, total;
+  size_t queue, tickets, tile_cnt, tile_cs, tile_peaks, tile_max, defer_list, spill, order, total;
+  int n_spill;
 };
 
+// Accumulators in HBM for events the tiled iterative finder defers (at most this many at once).
+constexpr int kSpillSlots = 8;
+
 WsLayout ws_layout(const Plan& pl, long long n_events);
+// Points the workspace fields of io into ws (laid out by wl) and clears the others.
+void bind_workspace(const Plan& pl, const WsLayout& wl, char* ws, FusedIO& io);
 void host_trig(int n_theta, TrigTable* t);
 BinMagic host_magic(int n_rho);
 

@@ -9,7 +9,12 @@
 // oldest request has waited flush_ns. Per slot: pinned gather -> H2D -> validate + fused kernel
 // (one CTA per event) -> peak packing -> D2H of counts, masks and packed peaks -> event; when
 // the event completes the loop copies each request's results into the caller's buffers and
-// stamps its completion time. Every wait is bounded.
+// stamps its completion time. Every wait is bounded: a batch that cannot be enqueued, or has
+// not completed after HOUGH_SERVE_BATCH_TIMEOUT_NS, finishes its requests with an error flag
+// and no results. The loop keeps a ring of per-batch timestamps and watches the gaps between
+// its own passes (and between the submissions of hough_serve_replay) for stalls.
+#include <time.h>
+
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -33,6 +38,42 @@ long long now_ns() {
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+long long thread_cpu_ns() {
+  timespec ts;
+  if (clock_gettime(CLOCK_THREAD_CPUTIME_ID, &ts) != 0) return 0;
+  return (long long)ts.tv_sec * 1000000000LL + ts.tv_nsec;
+}
+
+constexpr long long kStallNs = 1000000;  // a gap above 1 ms between passes is a stall
+
+// Gaps between consecutive ticks of one thread. The thread's CPU time is sampled about once a
+// millisecond, so the CPU time over a stall's window (the gap plus at most 1 ms before it)
+// tells whether the thread was busy (CPU time near the window) or not running (near zero).
+struct StallWatch {
+  long long t_last = 0, t_sample = 0, cpu_sample = 0;
+  long long stalls = 0, max_gap = 0, max_at = 0, max_cpu = 0;
+  void start(long long now) {
+    t_last = t_sample = now;
+    cpu_sample = thread_cpu_ns();
+  }
+  void tick(long long now) {
+    if (now - t_last > kStallNs) {
+      ++stalls;
+      const long long gap = now - t_last;
+      if (gap > max_gap) {
+        max_gap = gap;
+        max_at = t_last;
+        max_cpu = thread_cpu_ns() - cpu_sample;
+      }
+    }
+    t_last = now;
+    if (now - t_sample > kStallNs) {
+      t_sample = now;
+      cpu_sample = thread_cpu_ns();
+    }
+  }
+};
 
 struct Request {
   const int32_t* xy;
@@ -91,6 +132,9 @@ struct Slot {
   cudaEvent_t done = nullptr;
   std::vector<Request> reqs;
   bool busy = false;
+  bool dead = false;         // retired after a timeout or an unrecoverable error: never reused
+  long long t_launch = 0;    // when its batch was enqueued
+  long long rec = -1;        // its batch record (ring sequence number)
 };
 
 struct Server {
@@ -110,9 +154,20 @@ struct Server {
   std::atomic<int> error{0};
   long long submitted = 0, completed = 0;
   std::thread loop;
+  // tracing: batch records (ring), loop and submitter stall watches, under trace_mu
+  std::mutex trace_mu;
+  std::vector<hough_serve_batch_record> ring = std::vector<hough_serve_batch_record>(HOUGH_SERVE_RECORDS);
+  long long ring_next = 0;
+  long long passes = 0, batches = 0;
+  StallWatch loop_watch, submit_watch;
+  std::atomic<int> inject_failures{0};
 };
 
+hough_serve_batch_record& record_at(Server& S, long long seq) { return S.ring[(size_t)(seq % HOUGH_SERVE_RECORDS)]; }
+
 cudaError_t launch_batch(Server& S, Slot& sl) {
+  if (S.inject_failures.load() > 0 && S.inject_failures.fetch_sub(1) > 0)
+    return cudaErrorLaunchFailure;  // test hook: fail before anything is enqueued
   const SlotLayout& L = S.L;
   const size_t ne = sl.reqs.size();
   int64_t* hoff = (int64_t*)(sl.h + L.h_off);
@@ -142,11 +197,7 @@ cudaError_t launch_batch(Server& S, Slot& sl) {
   io.status = (int*)(sl.d + L.d_status);
   WsLayout wl = ws_layout(S.plan, (long long)ne);
   char* ws = sl.d + L.d_ws;
-  io.queue = (unsigned long long*)(ws + wl.queue);
-  io.tickets = S.plan.tiles > 1 ? (int*)(ws + wl.tickets) : nullptr;
-  io.tile_cnt = S.plan.tiles > 1 ? (int*)(ws + wl.tile_cnt) : nullptr;
-  io.tile_cs = S.plan.tiles > 1 ? (unsigned long long*)(ws + wl.tile_cs) : nullptr;
-  io.tile_peaks = S.plan.tiles > 1 ? (hough_peak*)(ws + wl.tile_peaks) : nullptr;
+  bind_workspace(S.plan, wl, ws, io);
   io.n_items = (long long)ne * S.plan.tiles;
   io.persistent = 0;
   e = launch_prep(io.off, io.n_events, nh, io.status, io.queue, io.tickets, nullptr, st);
@@ -204,27 +255,94 @@ void finish_batch(Server& S, Slot& sl, long long t_done) {
   S.cv.notify_all();
 }
 
+// Requests of a batch that produced no results (flag: HOUGH_F_TIMEOUT or HOUGH_F_LAUNCH_FAILED):
+// they finish with that status and nothing is copied to their output buffers.
+void fail_batch(Server& S, Slot& sl, long long t_done, int32_t flag) {
+  std::vector<hough_serve_result> out(sl.reqs.size());
+  for (size_t i = 0; i < sl.reqs.size(); ++i) {
+    hough_serve_result& o = out[i];
+    std::memset(&o, 0, sizeof(o));
+    o.id = sl.reqs[i].id;
+    o.status = flag;
+    o.t_arrival_ns = sl.reqs[i].t_arrival;
+    o.t_done_ns = t_done;
+  }
+  sl.reqs.clear();
+  std::lock_guard<std::mutex> lk(S.mu);
+  for (auto& o : out) S.results.push_back(o);
+  S.completed += (long long)out.size();
+  S.cv.notify_all();
+}
+
+// Waits (bounded) until the slot's stream has no work left: true if it drained.
+bool drain_slot(Server& S, Slot& sl) {
+  const long long t0 = now_ns();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(sl.stream);
+    if (q == cudaSuccess) return true;
+    if (q != cudaErrorNotReady) {
+      note_cuda_error(q);
+      S.error.store(HOUGH_ECUDA);
+      return false;
+    }
+    if (now_ns() - t0 > HOUGH_SERVE_BATCH_TIMEOUT_NS) {
+      S.error.store(HOUGH_ETIMEDOUT);
+      return false;
+    }
+    std::this_thread::yield();
+  }
+}
+
 void serve_loop(Server* Sp) {
   Server& S = *Sp;
   cudaSetDevice(S.device);
+  {
+    std::lock_guard<std::mutex> tk(S.trace_mu);
+    S.loop_watch.start(now_ns());
+  }
   while (S.running.load(std::memory_order_acquire)) {
     bool progress = false;
+    {
+      std::lock_guard<std::mutex> tk(S.trace_mu);
+      S.loop_watch.tick(now_ns());
+      ++S.passes;
+    }
     for (Slot& sl : S.slots) {
       if (!sl.busy) continue;
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaSuccess) {
-        finish_batch(S, sl, now_ns());
+        const long long t_seen = now_ns();
+        finish_batch(S, sl, t_seen);
+        const long long t_fin = now_ns();
+        {
+          std::lock_guard<std::mutex> tk(S.trace_mu);
+          if (sl.rec >= 0 && sl.rec + HOUGH_SERVE_RECORDS > S.ring_next) {
+            record_at(S, sl.rec).t_done_seen = t_seen;
+            record_at(S, sl.rec).t_finished = t_fin;
+          }
+        }
         sl.reqs.clear();
         sl.busy = false;
         progress = true;
-      } else if (q != cudaErrorNotReady) {
+      } else if (q != cudaErrorNotReady) {  // the batch failed on the device
         note_cuda_error(q);
         S.error.store(HOUGH_ECUDA);
+        fail_batch(S, sl, now_ns(), HOUGH_F_LAUNCH_FAILED);
+        sl.busy = false;
+        sl.dead = true;
+        progress = true;
+      } else if (now_ns() - sl.t_launch > HOUGH_SERVE_BATCH_TIMEOUT_NS) {
+        // its buffers may still be in use on the device: the slot is retired
+        S.error.store(HOUGH_ETIMEDOUT);
+        fail_batch(S, sl, now_ns(), HOUGH_F_TIMEOUT);
+        sl.busy = false;
+        sl.dead = true;
+        progress = true;
       }
     }
     Slot* free_slot = nullptr;
     for (Slot& sl : S.slots)
-      if (!sl.busy) {
+      if (!sl.busy && !sl.dead) {
         free_slot = &sl;
         break;
       }
@@ -247,12 +365,32 @@ void serve_loop(Server* Sp) {
         S.pending_hits -= hits;
         lk.unlock();
         if (!free_slot->reqs.empty()) {
-          const cudaError_t e = launch_batch(S, *free_slot);
+          Slot& sl = *free_slot;
+          const long long t_gather = now_ns();
+          const cudaError_t e = launch_batch(S, sl);
+          const long long t_launched = now_ns();
           if (e != cudaSuccess) {
+            // Nothing of this batch may report results: its requests finish with the flag once
+            // whatever was enqueued before the failure has drained from the slot's stream.
             note_cuda_error(e);
-            S.error.store(HOUGH_ECUDA);
+            if (!drain_slot(S, sl)) sl.dead = true;
+            fail_batch(S, sl, now_ns(), HOUGH_F_LAUNCH_FAILED);
+          } else {
+            sl.busy = true;
+            sl.t_launch = t_launched;
+            std::lock_guard<std::mutex> tk(S.trace_mu);
+            sl.rec = S.ring_next++;
+            hough_serve_batch_record& r = record_at(S, sl.rec);
+            r.t_gather = t_gather;
+            r.t_launched = t_launched;
+            r.t_done_seen = 0;
+            r.t_finished = 0;
+            r.n_events = (int32_t)sl.reqs.size();
+            r.slot = (int32_t)(&sl - S.slots.data());
+            r.n_hits = 0;
+            for (const Request& q : sl.reqs) r.n_hits += q.n_hits;
+            ++S.batches;
           }
-          free_slot->busy = true;
           progress = true;
         }
       }
@@ -400,26 +538,67 @@ int hough_serve_close(void* server) {
 }
 
 int hough_serve_replay(void* server, const int32_t* h_xy_pool, const int64_t* h_off_pool, int64_t pool_events,
-                       const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns) {
+                       const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns, uint8_t* h_mask_out,
+                       hough_peak* h_peaks_out) {
   if (!server || !h_off_pool || pool_events < 1 || !arrival_ns || n_requests < 0) return HOUGH_EINVAL;
   Server* S = (Server*)server;
   const long long t0 = now_ns();
   if (t_start_ns) *t_start_ns = t0;
-  for (int64_t i = 0; i < n_requests; ++i) {
+  StallWatch w;
+  w.start(t0);
+  int64_t m = 0;  // request i's mask offset
+  int rc = HOUGH_OK;
+  for (int64_t i = 0; i < n_requests && rc == HOUGH_OK; ++i) {
     const long long due = t0 + arrival_ns[i];
-    while (now_ns() < due) {
-    }
-    const int64_t e = i % pool_events;
-    int rc;
+    long long t;
+    while ((t = now_ns()) < due) w.tick(t);
+    w.tick(t);
+    const int64_t e = i % pool_events, nh = h_off_pool[e + 1] - h_off_pool[e];
+    uint8_t* mo = h_mask_out ? h_mask_out + m : nullptr;
+    hough_peak* po = h_peaks_out ? h_peaks_out + i * (int64_t)S->cfg.params.max_peaks : nullptr;
+    m += nh;
     // admission is refused while the queue is full; retry (for at most 10 s) keeping the
     // scheduled arrival time, so the wait shows up in the latency
-    while ((rc = submit_at(S, h_xy_pool + 2 * h_off_pool[e], h_off_pool[e + 1] - h_off_pool[e], i, nullptr,
-                           nullptr, due)) == HOUGH_EFULL) {
-      if (now_ns() - due > 10000000000LL) return HOUGH_ETIMEDOUT;
+    while ((rc = submit_at(S, h_xy_pool + 2 * h_off_pool[e], nh, i, mo, po, due)) == HOUGH_EFULL) {
+      if (now_ns() - due > 10000000000LL) {
+        rc = HOUGH_ETIMEDOUT;
+        break;
+      }
       std::this_thread::yield();
     }
-    if (rc) return rc;
   }
+  std::lock_guard<std::mutex> tk(S->trace_mu);
+  S->submit_watch = w;
+  return rc;
+}
+
+int hough_serve_trace(void* server, hough_serve_stats* out, hough_serve_batch_record* records, int32_t max_records,
+                      int32_t* n_records) {
+  if (!server || !out || max_records < 0 || (max_records > 0 && !records)) return HOUGH_EINVAL;
+  Server* S = (Server*)server;
+  std::lock_guard<std::mutex> tk(S->trace_mu);
+  std::memset(out, 0, sizeof(*out));
+  out->passes = S->passes;
+  out->batches = S->batches;
+  out->stall_ns = kStallNs;
+  out->loop_stalls = S->loop_watch.stalls;
+  out->loop_max_gap_ns = S->loop_watch.max_gap;
+  out->loop_max_gap_at = S->loop_watch.max_at;
+  out->loop_max_gap_cpu_ns = S->loop_watch.max_cpu;
+  out->submit_stalls = S->submit_watch.stalls;
+  out->submit_max_late_ns = S->submit_watch.max_gap;
+  out->submit_max_late_at = S->submit_watch.max_at;
+  out->submit_max_late_cpu_ns = S->submit_watch.max_cpu;
+  const long long avail = S->ring_next < HOUGH_SERVE_RECORDS ? S->ring_next : HOUGH_SERVE_RECORDS;
+  const long long n = avail < max_records ? avail : max_records;
+  for (long long i = 0; i < n; ++i) records[i] = record_at(*S, S->ring_next - n + i);
+  if (n_records) *n_records = (int32_t)n;
+  return HOUGH_OK;
+}
+
+int hough_serve_inject_launch_failures(void* server, int32_t n) {
+  if (!server || n < 0) return HOUGH_EINVAL;
+  ((Server*)server)->inject_failures.store(n);
   return HOUGH_OK;
 }
 

@@ -13,7 +13,10 @@
 // HOUGH_STATIC_SCRATCH_BYTES of it until the process exits. Host code cannot use the
 // symbol's name as an address: the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it. That first call should
-// therefore happen before any stream capture. Every call shares the same array and leaves its
+// therefore happen before any stream capture. The cached address belongs to the device's
+// primary context as it was at that first call: cudaDeviceReset destroys that context (and the
+// array with it), so a process that resets a device must not call this entry point on that
+// device afterwards. Every call shares the same array and leaves its
 // contents behind, so calls that overlap on the GPU (other streams, other host threads) race
 // and must be serialised by the caller. Everything that has to start at zero (the queue
 // counter and the per-event tile tickets) is cleared by the validation kernel of each call.
@@ -92,11 +95,7 @@ extern "C" int hough_run_batched_static(const int32_t* d_xy, int64_t n_hits, con
   io.nkept = d_nkept;
   io.checksum = (unsigned long long*)d_checksum;
   io.status = d_status;
-  io.queue = (unsigned long long*)(ws + wl.queue);
-  io.tickets = pl.tiles > 1 ? (int*)(ws + wl.tickets) : nullptr;
-  io.tile_cnt = pl.tiles > 1 ? (int*)(ws + wl.tile_cnt) : nullptr;
-  io.tile_cs = pl.tiles > 1 ? (unsigned long long*)(ws + wl.tile_cs) : nullptr;
-  io.tile_peaks = pl.tiles > 1 ? (hough_peak*)(ws + wl.tile_peaks) : nullptr;
+  bind_workspace(pl, wl, ws, io);
   io.n_items = n_events * (long long)pl.tiles;
   int* order = (int*)(ws + wl.order);
   cudaStream_t st = (cudaStream_t)stream;

@@ -261,8 +261,11 @@ __global__ void probe_kernel(int mode, int words, int iters, unsigned long long*
       w = (int)(mix64(z) % (unsigned long long)words);
     } else if (mode == 2) {
       w = ((warp * 16 + r) % rows) * 32;
-    } else {
-      w = (warp % rows) * 32 + lane;  // mode 3: each thread keeps adding to one word of its own bank
+    } else if (mode == 3) {
+      w = (warp % rows) * 32 + lane;  // each thread keeps adding to one word of its own bank
+    } else {  // mode 4: each lane on its own bank, at pseudo-random rows (the vote's pattern)
+      unsigned long long z = (unsigned long long)(blockIdx.x * 2654435761u + threadIdx.x * 40503u + r * 97u);
+      w = (int)(mix64(z) % (unsigned long long)rows) * 32 + lane;
     }
     p[r] = sm + w;
   }

@@ -1,5 +1,6 @@
 """Run as a child process by test_phase_timers.py: the phase-timer build of the library gives
-the oracle's results on a small batch and counts cycles in the phases that ran."""
+the oracle's results (counts, peak records, masks) on a small batch and counts cycles in the
+phases that ran."""
 import json
 import os
 import sys
@@ -31,6 +32,10 @@ def main():
     assert np.array_equal(out.npeaks.cpu().numpy(), ref.npeaks)
     assert np.array_equal(out.mask.cpu().numpy(), ref.mask)
     assert np.array_equal(out.nkept.cpu().numpy(), ref.nkept)
+    pk = np.ascontiguousarray(out.peaks.cpu().numpy().astype(np.int16)).view(oracle.PEAK_DTYPE).reshape(ev.n_events, -1)
+    for e in range(ev.n_events):  # the stored peak records, element by element
+        s = min(int(ref.npeaks[e]), 512)
+        assert np.array_equal(pk[e, :s], ref.peaks[e, :s]), e
     print(json.dumps({"enabled": enabled, "cycles": cyc, "lib": h.load()._name}))
 
 

@@ -46,17 +46,15 @@ def test_resolve_and_reject_params():
                 h.params(64, 64, 1, max_peaks=0), h.params(64, 64, 1, theta_tiles=100), h.params(64, 64, 1, block=33),
                 h.params(64, 64, 1, peak_mode=2), h.params(64, 64, 1, peak_mode=1, rel_den=0),
                 h.params(64, 64, 1, peak_mode=1, rel_num=3, rel_den=2),
-                h.params(64, 64, 1, peak_mode=1, nms_radius=32), h.params(64, 64, 1, peak_mode=1, nms_radius=-1),
-                h.params(256, 256, 16, peak_mode=1, theta_tiles=2)):
+                h.params(64, 64, 1, peak_mode=1, nms_radius=32), h.params(64, 64, 1, peak_mode=1, nms_radius=-1)):
         with pytest.raises(h.HoughError) as ei:
             h.resolve(bad)
         assert ei.value.code == h.EPARAM
-    # the iterative finder keeps the accumulator in one CTA
+    # the iterative finder: the whole accumulator in one CTA where it fits, else theta tiles
     r = h.resolve(h.params(256, 256, 16, max_peaks=4096, peak_mode=1, rel_num=1, rel_den=2, nms_radius=3))
     assert r.theta_tiles == 1 and r.peak_mode == 1 and r.rel_den == 2 and r.nms_radius == 3
-    with pytest.raises(h.HoughError) as ei:
-        h.resolve(h.params(512, 512, 20, peak_mode=1, rel_num=1, rel_den=2))
-    assert ei.value.code == h.ESMEM
+    assert h.resolve(h.params(256, 256, 16, peak_mode=1, theta_tiles=2)).theta_tiles == 2
+    assert h.resolve(h.params(512, 512, 20, peak_mode=1, rel_num=1, rel_den=2)).theta_tiles == 4
 
 
 def test_workspace_sizes(lib):
@@ -102,17 +100,31 @@ def test_phase_counters_off_in_the_default_build(lib):
     assert [name for name, _ in sorted(ids.items(), key=lambda kv: kv[1])] == list(h.PHASES)
 
 
+# theta tiles the plan takes for each accumulator shape (n_theta, n_rho), for both peak finders;
+# shapes not listed fit one CTA (one tile)
+PLAN_TILES = {(100, 1000): 2, (100, 1024): 2, (256, 1000): 4, (256, 1024): 4, (300, 1000): 5, (300, 1024): 5,
+              (512, 256): 2, (512, 1000): 8, (512, 1024): 8, (1000, 256): 4, (1000, 1000): 16, (1000, 1024): 16,
+              (1024, 256): 4, (1024, 1000): 16, (1024, 1024): 16}
+
+
 @pytest.mark.parametrize("nt", [4, 8, 64, 100, 256, 300, 512, 1000, 1024])
 @pytest.mark.parametrize("nr", [4, 63, 256, 1000, 1024])
 def test_plans_over_shapes(nt, nr):
-    """Every accumulator shape has a 3x3-finder plan (theta-tiled where one CTA cannot hold it).
-    The iterative finder needs the whole accumulator in one CTA: it plans untiled, or is refused
-    with HOUGH_ESMEM (the stepwise hough_peaks takes those shapes); up to 256 x 256 it fits."""
-    r = h.resolve(h.params(nt, nr, 16, 1, 1024))
-    assert r.theta_tiles >= 1 and r.block % 32 == 0 and 32 <= r.block <= 1024 and r.events_per_cta >= 1
-    q = h.params(nt, nr, 16, 1, 1024, peak_mode=h.PEAK_ITERATIVE, rel_num=1, rel_den=2, nms_radius=1)
-    try:
-        ri = h.resolve(q)
-        assert ri.theta_tiles == 1 and ri.block % 32 == 0
-    except h.HoughError as e:
-        assert e.code == -3 and nt * nr > 256 * 256
+    """Every accumulator shape has a plan for both peak finders, theta-tiled exactly where one CTA
+    cannot hold the accumulator (the iterative finder merges its tiles' candidates)."""
+    expect = PLAN_TILES.get((nt, nr), 1)
+    for kw in ({}, dict(peak_mode=h.PEAK_ITERATIVE, rel_num=1, rel_den=2, nms_radius=1)):
+        r = h.resolve(h.params(nt, nr, 16, 1, 1024, **kw))
+        assert r.theta_tiles == expect, (kw, r.theta_tiles)
+        assert r.block % 32 == 0 and 32 <= r.block <= 1024 and r.events_per_cta >= 1
+
+
+def test_probe_rejects_bad_arguments(lib):
+    """The shared-atomic probe checks its arguments before anything is launched (no GPU needed):
+    modes 0-4 exist, and the array must fit the shared-memory budget."""
+    sink = ctypes.c_void_p(256)  # never dereferenced: every call below is refused first
+    for mode, ctas, threads, smem, iters in ((5, 2, 1024, 98304, 10), (-1, 2, 1024, 98304, 10),
+                                            (0, 0, 1024, 98304, 10), (0, 2, 1000, 98304, 10),
+                                            (0, 2, 1024, 1024, 10), (0, 2, 1024, 1 << 20, 10), (4, 2, 1024, 98304, 0)):
+        assert lib.hough_probe_smem_atomics(mode, ctas, threads, smem, iters, sink, None) == h.EINVAL
+    assert lib.hough_probe_smem_atomics(0, 2, 1024, 98304, 10, None, None) == h.EINVAL

@@ -546,6 +546,88 @@ def test_iterative_stepwise_large_accumulator(h):
         assert np.array_equal(got[e][: min(n[e], 256)], exp[e][: min(n[e], 256)])
 
 
+# ---------------------------------------------------------------- iterative finder on theta tiles
+
+ITER_TILED = [  # (workload, events, n_theta, n_rho, threshold, rel_num, rel_den, nms_radius, max_peaks, tiles)
+    ("plain_paper", 40, 256, 256, 16, 1, 2, 3, 2048, 2),
+    ("plain_paper", 30, 256, 256, 16, 1, 2, 3, 2048, 4),   # windows across three tile edges
+    ("stress", 8, 512, 512, 20, 1, 2, 3, 16384, 4),        # the stress shape (13k candidates an event)
+    ("plain_paper", 20, 101, 63, 8, 1, 4, 2, 512, 3),      # odd N_theta: column tiles, no mirror pairs
+    ("plain_paper", 12, 1000, 1000, 12, 1, 2, 4, 1024, 16),  # the paper's discretisation
+    ("plain_small", 20, 64, 64, 6, 0, 1, 0, 300, 2),       # every cell >= T, no neighbourhood
+    ("batched", 16, 256, 256, 16, 1, 2, 64, 256, 8),       # windows wider than a tile (R = 64)
+]
+
+
+def run_iterative_tiled(h, xy_np, off_np, nt, nr, thr, num, den, R, mx, tiles):
+    op = oracle.params(nt, nr, thr, 1, mx, peak_mode=1, rel_num=num, rel_den=den, nms_radius=R)
+    ref = oracle.run(xy_np, off_np, op, threads=THREADS)
+    xy, off = torch.from_numpy(xy_np).cuda(), torch.from_numpy(off_np).cuda()
+    p = h.params(nt, nr, thr, 1, mx, theta_tiles=tiles, peak_mode=1, rel_num=num, rel_den=den, nms_radius=R)
+    assert h.resolve(p).theta_tiles == tiles
+    deferred = []
+    for batched in (False, True):
+        out = h.run(xy, off, p, checksum=True, batched=batched)
+        assert h.status(out.status) == ref.status
+        assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, off_np, checksum=out.checksum)
+        deferred.append(int(out.ws[8:12].view(torch.int32).item()))  # events the fallback kernel took
+    return ref, deferred
+
+
+@pytest.mark.parametrize("name,n,nt,nr,thr,num,den,R,mx,tiles", ITER_TILED)
+def test_iterative_tiled_matches_oracle(h, name, n, nt, nr, thr, num, den, R, mx, tiles):
+    """The paper's iterative finder with the accumulator split over theta tiles: each tile
+    publishes its candidates, the last tile of the event settles them; fused and batched
+    launches, outputs and accumulator checksums equal the oracle's."""
+    ev = gen.generate(gen.CONFIGS[name], n)
+    run_iterative_tiled(h, ev.xy, ev.off, nt, nr, thr, num, den, R, mx, tiles)
+
+
+def test_iterative_tiled_deferred_events(h):
+    """Events whose candidates do not fit the tiles' record slots (max_peaks 32 here) go to the
+    fallback kernel (HBM accumulator, the stepwise finder): results still equal the oracle's,
+    peak-list overflow included, and the fallback really ran."""
+    ev = gen.generate(gen.CONFIGS["plain_paper"], 24)
+    ref, deferred = run_iterative_tiled(h, ev.xy, ev.off, 256, 256, 16, 1, 2, 3, 32, 4)
+    assert min(deferred) > 0 and ref.status & 4  # some events deferred; some peak lists overflowed
+
+
+def test_iterative_tiled_cell_above_4095_votes(h):
+    """A cell above 4,095 votes (beyond the candidate keys' vote field) defers its event; its
+    neighbours in the batch take the tiles' candidate lists."""
+    ev = gen.generate(gen.CONFIGS["plain_paper"], 3)
+    a, b = int(ev.off[1]), int(ev.off[2])
+    xy = np.concatenate([ev.xy[:b], np.repeat(ev.xy[a:a + 1], 4200, axis=0), ev.xy[b:]])
+    off = ev.off.copy()
+    off[2:] += 4200
+    _, deferred = run_iterative_tiled(h, xy, off, 256, 256, 10, 1, 2, 2, 4096, 2)
+    assert deferred == [1, 1]  # the event with the 4,200-vote cells, in both launches
+
+
+@pytest.mark.parametrize("name,sample", [("stress", 40), ("paper_1000", 80)])
+def test_full_size_sampled_iterative_tiled(h, name, sample):
+    """The stress (512 x 512) and 1000 x 1000 workloads, whole, with the iterative finder (half the
+    maximum, radius 3) in the autotuned launch shape; the oracle recomputes a random sample."""
+    cfg = gen.CONFIGS[name]
+    ev = gen.generate(cfg, with_truth=False)
+    xy, off = dev(ev)
+    kw = dict(peak_mode=1, rel_num=1, rel_den=2, nms_radius=3)
+    p = cfg_params(h, cfg, **kw)
+    ns = min(ev.n_events, 2000)
+    p, _ = h.autotune(xy[: int(ev.off[ns])], off[: ns + 1], p)
+    assert h.resolve(p).theta_tiles > 1
+    out = h.run(xy, off, p, checksum=False, batched=True)
+    assert h.status(out.status) == 0
+    rng = np.random.default_rng(3)
+    events = np.sort(rng.choice(ev.n_events, size=sample, replace=False))
+    events[0] = 0
+    events[-1] = ev.n_events - 1
+    sxy, soff = sub_batch(ev.xy, ev.off, events)
+    ref = oracle.run(sxy, soff, oracle.params(cfg.n_theta, cfg.n_rho, cfg.threshold, cfg.keep_halfwidth,
+                                              cfg.max_peaks, **kw), threads=THREADS)
+    assert_event_outputs_equal(ref, out.npeaks, out.peaks, out.mask, out.nkept, ev.off, events=events)
+
+
 # ---------------------------------------------------------------- host-buffer path (pipelined chunks)
 
 @pytest.mark.parametrize("name,n,iterative", [("plain_paper", 300, False), ("batched", 9000, False),
