@@ -129,6 +129,14 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+T0 = time.perf_counter()
+
+
+def progress(what: str):
+    """Elapsed wall time of the run on stderr (the JSON line stays the only stdout line)."""
+    print(f"[bench {time.perf_counter() - T0:7.1f} s] {what}", file=sys.stderr, flush=True)
+
+
 def workload_config(cfg, n_events, args):
     """The workload a line is measured on: identical in the GPU arm and the reference arm."""
     return {"workload": cfg.name, "events_per_gpu": n_events, "n_theta": cfg.n_theta, "n_rho": cfg.n_rho,
@@ -217,10 +225,10 @@ def serve_stream(h, p, kw, pool, arrival, max_batch_hits=1 << 22):
     """One arrival stream through a server configured by kw: sustained events/s (completed over
     the span from the first scheduled arrival to the last result), latency percentiles from
     scheduled arrival to results in host memory, device flags, and the loop's stall watch."""
-    with h.Server(p, max_batch_hits=max_batch_hits, **kw) as srv:
-        t0 = srv.replay(pool.xy, pool.off, arrival)
+    res = h.Server.result_array(len(arrival))  # written now: the loop faults in no pages
+    with h.Server(p, max_batch_hits=max_batch_hits, queue_capacity=1 << 16, **kw) as srv:
+        t0 = srv.replay(pool.xy, pool.off, arrival, results_out=res)
         srv.drain(300)
-        res = srv.poll_numpy(len(arrival) + 16)
         stats, rec = srv.trace()
     lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e3
     span = (res["t_done_ns"].max() - t0) / 1e9 if len(res) else float("nan")
@@ -228,10 +236,8 @@ def serve_stream(h, p, kw, pool, arrival, max_batch_hits=1 << 22):
            "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
            "completed": int(len(res)), "flags": int(np.bitwise_or.reduce(res["status"])),
            "batches": stats["batches"], "mean_batch_events": float(rec["n_events"].mean()) if len(rec) else None,
-           "loop_stalls": stats["loop_stalls"], "loop_max_gap_us": stats["loop_max_gap_ns"] / 1e3,
-           "loop_max_gap_cpu_us": stats["loop_max_gap_cpu_ns"] / 1e3, "submit_stalls": stats["submit_stalls"],
-           "submit_max_late_us": stats["submit_max_late_ns"] / 1e3,
-           "submit_max_late_cpu_us": stats["submit_max_late_cpu_ns"] / 1e3}
+           "stalls": {w: dict(stats[w], max_gap_at_ms=(stats[w]["max_gap_at"] - t0) / 1e6 if stats[w]["count"] else None)
+                      for w in ("loop", "submit")}}
     if len(rec):  # where a micro-batch's time goes (medians over the stream's most recent batches)
         out["batch_us"] = {"gather_and_enqueue": float(np.median(rec["t_launched"] - rec["t_gather"]) / 1e3),
                            "device_and_copies": float(np.median(rec["t_done_seen"] - rec["t_launched"]) / 1e3),
@@ -243,8 +249,8 @@ SERVED = dict(slots=4, max_batch_events=256, flush_us=50.0)
 PLAIN_1000 = dict(slots=1, max_batch_events=1000, flush_us=0.0)
 
 
-def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000, seed=11, sat_events=400_000,
-                    sat_rates=(1_000_000, 2_000_000, 4_000_000), sat_seconds=0.5):
+def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000, seed=11, sat_events=300_000,
+                    sat_rates=(1_000_000, 2_000_000, 4_000_000), sat_seconds=0.25):
     """Continuous-batching server (4 slots, micro-batches of at most 256 events, launched after
     flush_us) vs plain per-batch launches of 1,000 events (one batch in flight, launched when
     full), both fed the same Poisson arrival streams. Streams at the offered rates, streams past
@@ -256,6 +262,7 @@ def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000,
     arms = (("served", served), ("plain_1000", PLAIN_1000))
     streams = []
     for rate, secs in [(r, seconds) for r in rates] + [(r, sat_seconds) for r in sat_rates]:
+        progress(f"serving stream {rate} events/s")
         n = int(rate * secs)
         arrival = np.cumsum(rng.exponential(1e9 / rate, size=n)).astype(np.int64)
         row = {"offered_events_per_s": rate, "seconds": secs, "events": n, "flush_us": flush_us}
@@ -264,7 +271,8 @@ def measure_serving(h, cfg, p, rates, seconds, flush_us=50.0, pool_events=20000,
         streams.append(row)
     closed = {}
     for name, kw in arms:
-        closed[name] = serve_stream(h, p, kw, pool, np.zeros(sat_events, np.int64))
+        if sat_events:
+            closed[name] = serve_stream(h, p, kw, pool, np.zeros(sat_events, np.int64))
     # the highest offered rate whose p99 stays within 200 us, per arm
     best = {}
     for name, _ in arms:
@@ -516,6 +524,8 @@ def main():
                     help="serving loop: longest wait of a request before its partial micro-batch is launched")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-phase", action="store_true", help="skip the vote-phase fraction (phase-timer child run)")
+    ap.add_argument("--serve-only", type=int, default=0,
+                    help="only the serving streams, this many times over (stall study); one JSON line per repeat")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape instead of the autotuner")
     ap.add_argument("--tune-events", type=int, default=10000, help="events of the batch the autotuner times")
     ap.add_argument("--shape", default="", help="fixed launch shape 'theta_tiles,block,events_per_cta' (profiling)")
@@ -538,6 +548,17 @@ def main():
         return run_sweep(args, cfg)
     if args.phase_split:
         return run_phase_split(args, cfg)
+    if args.serve_only:
+        import torch
+        import paper_2607_04067_gb300 as h
+        torch.cuda.set_device(0)
+        scfg = gen.CONFIGS["served"]
+        sp = h.params(scfg.n_theta, scfg.n_rho, scfg.threshold, scfg.keep_halfwidth, scfg.max_peaks)
+        for rep in range(args.serve_only):
+            res = measure_serving(h, scfg, sp, (50_000, 200_000, 400_000), args.serve_seconds, args.serve_flush_us,
+                                  seed=11 + rep, sat_rates=(), sat_events=0)
+            print(json.dumps({"metric": "served streams", "repeat": rep, **res}), flush=True)
+        return 0
 
     import torch
     import paper_2607_04067_gb300 as h
@@ -585,6 +606,7 @@ def main():
     stream.synchronize()
     flags = h.status(out.status, stream)
 
+    progress("warm-up done")
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -613,6 +635,7 @@ def main():
     total_events = n_events * ws * args.steps
     value = total_events / (elapsed * 1e-3)
 
+    progress("timed steps done")
     # end to end through the host-buffer entry point (pinned host in, host results out)
     xy_h = torch.from_numpy(ev.xy).pin_memory()
     off_h = torch.from_numpy(ev.off).pin_memory()
@@ -641,6 +664,7 @@ def main():
             dist.destroy_process_group()
         return
 
+    progress("end to end done")
     peaks_meas, peaks_kind = measured_peaks()
     votes = ev.n_hits * cfg.n_theta
     kern = float(np.mean(kern_ms))
@@ -675,10 +699,12 @@ def main():
                "single_thread": {"value": v1, "unit": "events/s", "cores": 1,
                                  "sample": f"first {n1} events of this batch ({dt1:.1f} s on 1 thread)"}}
 
+    progress("oracle and parity done")
     vote_phase = None
     if not args.no_phase:
         vote_phase = vote_phase_fraction(args, cfg, ceiling["lane_bank"], sms, clk.get("sm_mhz"))
 
+    progress("vote phase done")
     served = None
     if not args.no_serve:
         scfg = gen.CONFIGS["served"]
@@ -686,6 +712,7 @@ def main():
                                                    scfg.max_peaks), (50_000, 200_000, 400_000), args.serve_seconds,
                                  args.serve_flush_us)
 
+    progress("serving done")
     import oracle
     rc, rs = oracle.metrics(out.mask.cpu().numpy(), ev.truth) if ev.truth is not None else (None, None)
     lane = ceiling["lane_bank"]
@@ -726,6 +753,7 @@ def main():
                     "track_finding": track_finding(h, cfg, out, p, 0, args.physics_events)},
         "cpu_baseline": cpu,
     }
+    progress("physics done")
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -237,7 +237,9 @@ typedef struct hough_serve_config {
   int32_t max_batch_events; /* events per micro-batch, >= 1 */
   int64_t max_batch_hits;   /* hits per micro-batch, >= 1 (also the largest admissible event) */
   int64_t flush_ns;         /* longest wait of a request before its partial batch is launched */
-  int32_t queue_capacity;   /* requests waiting for a slot before submit refuses (HOUGH_EFULL) */
+  int32_t queue_capacity;   /* requests waiting for a slot before submit refuses (HOUGH_EFULL); the
+                               ring of results not yet polled holds queue_capacity plus the
+                               in-flight requests, and a request is admitted only with room there */
   int32_t reserved;
 } hough_serve_config;
 
@@ -265,7 +267,9 @@ int hough_serve_buffer_sizes(const hough_serve_config* c, size_t* device_bytes, 
 
 /* Starts a server on the current device. d_buf (device) and h_pinned (page-locked host
  * memory) are caller-owned, 256-byte aligned and must outlive the server. *server receives
- * an opaque handle. A host thread owned by the server runs the loop until hough_serve_close. */
+ * an opaque handle. A host thread owned by the server runs the loop until hough_serve_close.
+ * The server's own host memory (request queue, results ring, per-slot lists) is allocated and
+ * written here, once: the serving path neither allocates nor touches fresh pages. */
 int hough_serve_open(const hough_serve_config* c, void* d_buf, size_t d_bytes, void* h_pinned, size_t h_bytes,
                      void** server);
 
@@ -288,11 +292,13 @@ int hough_serve_drain(void* server, int64_t timeout_ns);
  * t0 + arrival_ns[i] (busy wait), t0 written to *t_start_ns. A refused admission is retried
  * for up to 10 s with the same scheduled arrival time. Results are copied out when the
  * buffers are given (each nullable): request i's kept mask to h_mask_out + m_i, where m_i is
- * the sum of the hit counts of requests 0 .. i-1, and its stored peaks to
- * h_peaks_out + i * max_peaks. */
+ * the sum of the hit counts of requests 0 .. i-1, its stored peaks to h_peaks_out + i * max_peaks,
+ * and its result record to h_results_out[i] (then it does not go to the results ring and
+ * hough_serve_poll does not return it; write the array once beforehand, so that the loop does
+ * not fault its pages in). */
 int hough_serve_replay(void* server, const int32_t* h_xy_pool, const int64_t* h_off_pool, int64_t pool_events,
                        const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns, uint8_t* h_mask_out,
-                       hough_peak* h_peaks_out);
+                       hough_peak* h_peaks_out, hough_serve_result* h_results_out);
 
 /* Stops the loop, waits for the streams and releases the handle. */
 int hough_serve_close(void* server);
@@ -311,22 +317,28 @@ typedef struct hough_serve_batch_record {
 
 #define HOUGH_SERVE_RECORDS 65536
 
-/* Health of the serving loop and of hough_serve_replay's submitter, for finding stalls: a
- * pass of the loop (or a submission) that starts more than stall_ns after the previous one is
- * a stall, recorded with its wall time and the CPU time the thread used meanwhile (near the
- * wall time: the thread was busy, e.g. in page faults; near zero: it was not running). */
+/* Stalls of one thread: gaps of more than stall_ns between its consecutive ticks (passes of the
+ * serving loop, or iterations of hough_serve_replay's submitter, which ticks while it waits for
+ * the next scheduled arrival). For the longest gap, the thread's usage over its window (the gap
+ * plus at most 1 ms before it, sampled with getrusage): CPU time near the window means it was
+ * busy (system time and minor faults: in the kernel, e.g. faulting pages in); near zero that it
+ * was not running (voluntary switches: blocked; involuntary ones: preempted). */
+typedef struct hough_serve_stall {
+  int64_t count;
+  int64_t max_gap_ns;
+  int64_t max_gap_at; /* when the longest gap began (steady clock, ns) */
+  int64_t user_ns, sys_ns;
+  int64_t minor_faults;
+  int64_t voluntary_switches, involuntary_switches;
+} hough_serve_stall;
+
+/* Health of the serving loop and of hough_serve_replay's submitter, for finding stalls. */
 typedef struct hough_serve_stats {
-  int64_t passes;            /* passes of the serving loop */
-  int64_t batches;           /* micro-batches launched */
-  int64_t stall_ns;          /* threshold (1 ms) */
-  int64_t loop_stalls;       /* gaps between loop passes above stall_ns */
-  int64_t loop_max_gap_ns;   /* the longest gap, */
-  int64_t loop_max_gap_at;   /* when it began (steady clock), */
-  int64_t loop_max_gap_cpu_ns; /* and the loop thread's CPU time during it */
-  int64_t submit_stalls;     /* replay: submissions more than stall_ns behind their schedule */
-  int64_t submit_max_late_ns; /* replay: the latest submission, behind its schedule by this, */
-  int64_t submit_max_late_at; /* at this scheduled time, */
-  int64_t submit_max_late_cpu_ns; /* and the submitting thread's CPU time meanwhile */
+  int64_t passes;           /* passes of the serving loop */
+  int64_t batches;          /* micro-batches launched */
+  int64_t stall_ns;         /* threshold (1 ms) */
+  hough_serve_stall loop;   /* the serving loop's thread */
+  hough_serve_stall submit; /* the thread of the last hough_serve_replay */
 } hough_serve_stats;
 
 /* Copies the loop's statistics into *out, and up to max_records of the most recent batch

@@ -50,12 +50,19 @@ class ServeConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-class ServeStats(ctypes.Structure):
+class ServeStall(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
-        "passes", "batches", "stall_ns", "loop_stalls", "loop_max_gap_ns", "loop_max_gap_at", "loop_max_gap_cpu_ns",
-        "submit_stalls", "submit_max_late_ns", "submit_max_late_at", "submit_max_late_cpu_ns")]
+        "count", "max_gap_ns", "max_gap_at", "user_ns", "sys_ns", "minor_faults", "voluntary_switches",
+        "involuntary_switches")]
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int64), ("batches", ctypes.c_int64), ("stall_ns", ctypes.c_int64),
+                ("loop", ServeStall), ("submit", ServeStall)]
+
+
+RESULT_DTYPE = [("id", "<i8"), ("status", "<i4"), ("npeaks", "<i4"), ("nkept", "<i4"), ("reserved", "<i4"),
+                ("t_arrival_ns", "<i8"), ("t_done_ns", "<i8")]
 BATCH_RECORD_DTYPE = [("t_gather", "<i8"), ("t_launched", "<i8"), ("t_done_seen", "<i8"), ("t_finished", "<i8"),
                       ("n_hits", "<i8"), ("n_events", "<i4"), ("slot", "<i4")]
 SERVE_RECORDS = 65536
@@ -132,7 +139,7 @@ def load(build: bool = True):
                 "hough_serve_submit": [vp, vp, i64, i64, vp, vp],
                 "hough_serve_poll": [vp, vp, i32, ctypes.POINTER(i32)],
                 "hough_serve_drain": [vp, i64],
-                "hough_serve_replay": [vp, vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp, vp],
+                "hough_serve_replay": [vp, vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp, vp, vp],
                 "hough_serve_close": [vp],
                 "hough_serve_trace": [vp, ctypes.POINTER(ServeStats), vp, i32, ctypes.POINTER(i32)],
                 "hough_serve_inject_launch_failures": [vp, i32],
@@ -411,7 +418,7 @@ class Server:
     torch tensors owned by this object; the loop itself is a native thread in the library."""
 
     def __init__(self, p: Params, slots: int = 4, max_batch_events: int = 256, max_batch_hits: int = 1 << 20,
-                 flush_us: float = 50.0, queue_capacity: int = 1 << 20, device="cuda"):
+                 flush_us: float = 50.0, queue_capacity: int = 1 << 16, device="cuda"):
         torch = _torch()
         self.cfg = ServeConfig(p, slots, max_batch_events, max_batch_hits, int(flush_us * 1000), queue_capacity, 0)
         lib = load()
@@ -447,9 +454,7 @@ class Server:
 
     def poll_numpy(self, max_results: int = 1 << 22):
         import numpy as np
-        dt = np.dtype([("id", "<i8"), ("status", "<i4"), ("npeaks", "<i4"), ("nkept", "<i4"), ("reserved", "<i4"),
-                       ("t_arrival_ns", "<i8"), ("t_done_ns", "<i8")])
-        out = np.zeros(max_results, dt)
+        out = np.zeros(max_results, np.dtype(RESULT_DTYPE))
         n = ctypes.c_int32()
         rc = load().hough_serve_poll(self.handle, ctypes.c_void_p(out.ctypes.data), max_results, ctypes.byref(n))
         if rc:
@@ -459,17 +464,28 @@ class Server:
     def drain(self, timeout_s: float = 30.0):
         _check("hough_serve_drain", load().hough_serve_drain(self.handle, int(timeout_s * 1e9)))
 
-    def replay(self, xy_pool, off_pool, arrival_ns, mask_out=None, peaks_out=None) -> int:
+    def replay(self, xy_pool, off_pool, arrival_ns, mask_out=None, peaks_out=None, results_out=None) -> int:
         """Submits request i = pool event i mod n at its scheduled time; returns t0 (ns). With
         mask_out (uint8, the requests' hit counts summed) and peaks_out (int16 [requests,
-        max_peaks, 4]) numpy arrays, each request's results are copied there."""
+        max_peaks, 4]) numpy arrays, each request's results are copied there; with results_out
+        (result_array(n)) request i's result record goes to results_out[i] instead of poll()."""
         t0 = ctypes.c_int64()
         mo = None if mask_out is None else ctypes.c_void_p(mask_out.ctypes.data)
         po = None if peaks_out is None else ctypes.c_void_p(peaks_out.ctypes.data)
+        ro = None if results_out is None else ctypes.c_void_p(results_out.ctypes.data)
         _check("hough_serve_replay", load().hough_serve_replay(
             self.handle, ctypes.c_void_p(xy_pool.ctypes.data), ctypes.c_void_p(off_pool.ctypes.data),
-            len(off_pool) - 1, ctypes.c_void_p(arrival_ns.ctypes.data), len(arrival_ns), ctypes.byref(t0), mo, po))
+            len(off_pool) - 1, ctypes.c_void_p(arrival_ns.ctypes.data), len(arrival_ns), ctypes.byref(t0), mo, po,
+            ro))
         return t0.value
+
+    @staticmethod
+    def result_array(n: int):
+        """A numpy array of n result records, written once (its pages faulted in now)."""
+        import numpy as np
+        out = np.empty(n, np.dtype(RESULT_DTYPE))
+        out.view(np.uint8).fill(0)
+        return out
 
     def trace(self, max_records: int = 65536):
         """(stats dict, numpy records of the most recent micro-batches, oldest first)."""
@@ -480,7 +496,9 @@ class Server:
         _check("hough_serve_trace", load().hough_serve_trace(self.handle, ctypes.byref(st),
                                                              ctypes.c_void_p(rec.ctypes.data), max_records,
                                                              ctypes.byref(n)))
-        return {k: int(getattr(st, k)) for k, _ in ServeStats._fields_}, rec[: n.value]
+        stall = lambda w: {k: int(getattr(w, k)) for k, _ in ServeStall._fields_}  # noqa: E731
+        return ({"passes": int(st.passes), "batches": int(st.batches), "stall_ns": int(st.stall_ns),
+                 "loop": stall(st.loop), "submit": stall(st.submit)}, rec[: n.value])
 
     def inject_launch_failures(self, n: int):
         """Test hook: the next n micro-batch launches fail on the host before anything is enqueued."""

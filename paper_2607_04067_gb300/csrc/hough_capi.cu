@@ -114,9 +114,8 @@ static bool layout(Plan& pl) {
   {
     int iter_words = 0;
     if (it_whole) {
-      // the candidate bitmap, column starts and candidate keys (or the one-pass-per-peak form's
-      // slice maxima)
-      const int cand_words = wpad * pl.nrb + ((pl.n_theta + 4) & ~3) + pl.iter_cap;
+      // candidate keys, then 2 state bits a cell (also room for the walk's 1-bit bitmap)
+      const int cand_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 15) / 16;
       iter_words = iter_scratch_words(pl.n_theta, pl.n_rho, kIterSliceRows);
       if (pl.iter_cap > 0 && cand_words > iter_words) iter_words = cand_words;
     }
@@ -135,7 +134,7 @@ static bool layout(Plan& pl) {
     // [off_acc, off_unres); the deferred kernel's finder (scratch, then a bitmap of every cell)
     // below the trig table
     const int free_bytes = pl.off_unres - pl.off_acc - 4 * ((pl.n_theta + 4) & ~3);
-    pl.merge_cap = std::min(65535, free_bytes / 5) & ~15;  // candidate indices fit 16 bits
+    pl.merge_cap = std::min(65520, free_bytes / 5) & ~15;  // key and state a candidate (16-bit indices)
     const int avail = pl.off_trig / 4, gone = (pl.n_theta * pl.n_rho + 31) / 32;
     int sh = kIterSliceRows;
     while (sh < pl.n_rho && iter_scratch_words(pl.n_theta, pl.n_rho, sh) + gone > avail) sh *= 2;

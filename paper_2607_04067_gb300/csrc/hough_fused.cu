@@ -1432,78 +1432,6 @@ __device__ int resolve_sparse(const Plan& pl, const SparseCands& s, int keys_roo
   return nk;
 }
 
-// The iterative finder on a whole accumulator in the CTA (one tile). The maximum gives the
-// threshold tq = max(T, ceil(rel max)); the cells >= tq are marked in a bitmap (pbits) and
-// listed in raster order, a thread per column, with their column starts; the accumulator's
-// shared memory is then the work area of the resolution. Events whose maximum exceeds the keys'
-// 12-bit vote field, or with more candidates than the plan's iter_cap, take the one-pass-per-peak
-// form on the accumulator instead. Records in extraction order; returns the count.
-template <bool A32, class Cells>
-__device__ int iterative_whole(const Plan& pl, Cells& cells, unsigned char* smem, ItemShared& sh, hough_peak* dst) {
-  const int NT = pl.n_theta, NR = pl.n_rho, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5,
-            nwarps = blockDim.x >> 5, bd = blockDim.x;
-  uint32_t* acc = reinterpret_cast<uint32_t*>(smem + pl.off_acc);
-  uint32_t* pbits = reinterpret_cast<uint32_t*>(smem + pl.off_pbits);
-  const int bm_words = pl.groups * 32 * pl.nrb;
-  int* colstart = reinterpret_cast<int*>(pbits + bm_words);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(colstart + ((NT + 4) & ~3));
-  if (tid == 0) sh.it_max = 0;
-  __syncthreads();
-  {  // the maximum (a warp takes rows, its lanes words of two columns, or columns)
-    int m = 0;
-    if constexpr (Cells::kPairs) {
-      for (int k = warp; k < NR; k += nwarps)
-        for (int w = lane; w < cells.words(); w += 32) {
-          const uint32_t x = cells.word(w, k);
-          m = max(m, (int)max(x & 0xffffu, x >> 16));
-        }
-    } else {
-      for (int k = warp; k < NR; k += nwarps)
-        for (int j = lane; j < NT; j += 32) m = max(m, cells.get(j, k));
-    }
-    m = __reduce_max_sync(kFull, m);
-    if (lane == 0 && m) atomicMax(&sh.it_max, m);
-  }
-  __syncthreads();
-  HOUGH_PHASE(HOUGH_PHASE_IT_MAX);
-  const int amax = sh.it_max;
-  const long long need = ((long long)pl.rel_num * amax + pl.rel_den - 1) / pl.rel_den;
-  const int tq = (int)max((long long)pl.threshold, need);
-  int C = -1;
-  if (amax <= 4095 && pl.iter_cap > 0) {
-    tile_candidate_bits<A32>(pl, acc, pbits, pl.mp ? NT >> 1 : 0, NT, tq);
-    __syncthreads();
-    for (int j = tid; j < NT; j += bd) {
-      int c = 0;
-      for (int w = 0; w < pl.nrb; ++w) c += __popc(pbits[j * pl.nrb + w]);
-      colstart[j] = c;
-    }
-    colstart[NT] = 0;
-    __syncthreads();
-    C = block_exscan(colstart, NT + 1, sh.tmp);
-    if (C <= pl.iter_cap) {
-      for (int j = tid; j < NT; j += bd) {
-        int pos = colstart[j];
-        for (int w = 0; w < pl.nrb; ++w) {
-          uint32_t bits = pbits[j * pl.nrb + w];
-          while (bits) {
-            const int k = (w << 5) + __ffs(bits) - 1;
-            bits &= bits - 1u;
-            keys[pos++] = cand_key(cells.get(j, k), j, k);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  HOUGH_PHASE(HOUGH_PHASE_IT_COLLECT);
-  if (C < 0 || C > pl.iter_cap)  // uniform
-    return extract_iterative_passes(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den,
-                                    pl.nms_radius, pl.max_peaks, pbits, dst, sh.tmp);
-  const SparseCands sc{keys, colstart, C};
-  return resolve_sparse(pl, sc, pl.iter_cap, reinterpret_cast<unsigned char*>(acc), pl.region_bytes, dst, sh);
-}
-
 // The event's peaks from its tiles' candidate lists, in the last tile CTA of the event. The
 // event's threshold tq = max(T, ceil(rel max)) comes from the tiles' maxima. The candidates (cells
 // >= tq) are gathered in raster order, with the first candidate of every column (colstart), into
@@ -1777,7 +1705,10 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       }
       __syncthreads();
       HOUGH_PHASE(HOUGH_PHASE_SCAN);
-      return iterative_whole<A32>(pl, cells, smem, sh, io.peaks + e * (long long)maxp);
+      HOUGH_PHASE(HOUGH_PHASE_SCAN);
+      return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
+                               maxp, pbits, pl.iter_cap, nullptr, (NT * NR + 15) >> 4,
+                               io.peaks + e * (long long)maxp, sh.tmp);
     };
     total = pl.mp ? iterative(FusedCells<A32, true>{acc, Wd, nrp, pl.rows_phys})
                   : iterative(FusedCells<A32, false>{acc, Wd, nrp, pl.rows_phys});

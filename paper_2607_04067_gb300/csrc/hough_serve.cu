@@ -13,13 +13,13 @@
 // not completed after HOUGH_SERVE_BATCH_TIMEOUT_NS, finishes its requests with an error flag
 // and no results. The loop keeps a ring of per-batch timestamps and watches the gaps between
 // its own passes (and between the submissions of hough_serve_replay) for stalls.
+#include <sys/resource.h>
 #include <time.h>
 
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
-#include <deque>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -39,38 +39,59 @@ long long now_ns() {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-long long thread_cpu_ns() {
-  timespec ts;
-  if (clock_gettime(CLOCK_THREAD_CPUTIME_ID, &ts) != 0) return 0;
-  return (long long)ts.tv_sec * 1000000000LL + ts.tv_nsec;
+// Resource usage of the calling thread: user and system CPU time (ns), minor page faults,
+// voluntary context switches (the thread blocked) and involuntary ones (it was preempted).
+struct ThreadUsage {
+  long long user_ns = 0, sys_ns = 0, minflt = 0, nvcsw = 0, nivcsw = 0;
+};
+
+ThreadUsage thread_usage() {
+  ThreadUsage u;
+  rusage r;
+  if (getrusage(RUSAGE_THREAD, &r) != 0) return u;
+  u.user_ns = (long long)r.ru_utime.tv_sec * 1000000000LL + (long long)r.ru_utime.tv_usec * 1000LL;
+  u.sys_ns = (long long)r.ru_stime.tv_sec * 1000000000LL + (long long)r.ru_stime.tv_usec * 1000LL;
+  u.minflt = r.ru_minflt;
+  u.nvcsw = r.ru_nvcsw;
+  u.nivcsw = r.ru_nivcsw;
+  return u;
 }
 
 constexpr long long kStallNs = 1000000;  // a gap above 1 ms between passes is a stall
 
-// Gaps between consecutive ticks of one thread. The thread's CPU time is sampled about once a
-// millisecond, so the CPU time over a stall's window (the gap plus at most 1 ms before it)
-// tells whether the thread was busy (CPU time near the window) or not running (near zero).
+// Gaps between consecutive ticks of one thread. The thread's resource usage is sampled about once
+// a millisecond, so its usage over a stall's window (the gap plus at most 1 ms before it) tells
+// what the thread did meanwhile: CPU time near the window means it was busy (system time and
+// page faults: in the kernel), near zero that it was not running (voluntary switches: blocked;
+// involuntary ones: preempted).
 struct StallWatch {
-  long long t_last = 0, t_sample = 0, cpu_sample = 0;
-  long long stalls = 0, max_gap = 0, max_at = 0, max_cpu = 0;
+  long long t_last = 0, t_sample = 0;
+  ThreadUsage u_sample;
+  long long stalls = 0, max_gap = 0, max_at = 0;
+  ThreadUsage max_use;  // usage over the longest stall's window
   void start(long long now) {
     t_last = t_sample = now;
-    cpu_sample = thread_cpu_ns();
+    u_sample = thread_usage();
   }
   void tick(long long now) {
     if (now - t_last > kStallNs) {
       ++stalls;
       const long long gap = now - t_last;
       if (gap > max_gap) {
+        const ThreadUsage u = thread_usage();
         max_gap = gap;
         max_at = t_last;
-        max_cpu = thread_cpu_ns() - cpu_sample;
+        max_use.user_ns = u.user_ns - u_sample.user_ns;
+        max_use.sys_ns = u.sys_ns - u_sample.sys_ns;
+        max_use.minflt = u.minflt - u_sample.minflt;
+        max_use.nvcsw = u.nvcsw - u_sample.nvcsw;
+        max_use.nivcsw = u.nivcsw - u_sample.nivcsw;
       }
     }
     t_last = now;
     if (now - t_sample > kStallNs) {
       t_sample = now;
-      cpu_sample = thread_cpu_ns();
+      u_sample = thread_usage();
     }
   }
 };
@@ -81,7 +102,34 @@ struct Request {
   int64_t id;
   uint8_t* mask_out;
   hough_peak* peaks_out;
-  long long t_arrival;  // scheduled arrival (ns, steady clock)
+  hough_serve_result* result_out;  // nullable: the result goes here instead of the results ring
+  long long t_arrival;             // scheduled arrival (ns, steady clock)
+};
+
+// Fixed-capacity FIFO whose storage is allocated and written once at construction, so that
+// pushing and popping never allocate or touch a fresh page: on the serving path a page fault
+// can block a thread for tens of milliseconds while the kernel compacts or migrates memory.
+template <class T>
+struct Ring {
+  std::vector<T> buf;
+  size_t head = 0, count = 0;
+  explicit Ring(size_t cap = 1) : buf(cap > 0 ? cap : 1) {}
+  bool empty() const { return count == 0; }
+  size_t size() const { return count; }
+  size_t capacity() const { return buf.size(); }
+  T& front() { return buf[head]; }
+  void pop_front() {
+    head = head + 1 == buf.size() ? 0 : head + 1;
+    --count;
+  }
+  bool push_back(const T& x) {
+    if (count == buf.size()) return false;
+    size_t at = head + count;
+    if (at >= buf.size()) at -= buf.size();
+    buf[at] = x;
+    ++count;
+    return true;
+  }
 };
 
 // Per-slot carve-up of the device and pinned host buffers.
@@ -130,7 +178,8 @@ struct Slot {
   hough_peak* dense_mapped = nullptr;  // device view of the pinned dense-peak area, when mapped
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  std::vector<Request> reqs;
+  std::vector<Request> reqs;            // capacity max_batch_events, reserved at open
+  std::vector<hough_serve_result> out;  // the batch's results, likewise
   bool busy = false;
   bool dead = false;         // retired after a timeout or an unrecoverable error: never reused
   long long t_launch = 0;    // when its batch was enqueued
@@ -146,9 +195,10 @@ struct Server {
   std::vector<Slot> slots;
   std::mutex mu;                  // guards pending, results, counters
   std::condition_variable cv;     // wakes drain() waiters
-  std::deque<Request> pending;
+  Ring<Request> pending;          // queue_capacity requests waiting for a slot
   int64_t pending_hits = 0;
-  std::deque<hough_serve_result> results;
+  Ring<hough_serve_result> results;  // finished requests not yet polled
+  long long outstanding = 0;      // admitted requests whose result has not reached the caller
   std::atomic<bool> running{false};
   std::atomic<bool> draining{false};
   std::atomic<int> error{0};
@@ -223,7 +273,22 @@ cudaError_t launch_batch(Server& S, Slot& sl) {
   return e;
 }
 
-// Results of a finished slot into the callers' buffers and the result queue.
+// Results of a finished slot into the callers' buffers and the results ring (or each request's
+// own result record). Admission keeps room in the ring for every admitted request.
+void deliver(Server& S, Slot& sl) {
+  std::lock_guard<std::mutex> lk(S.mu);
+  for (size_t i = 0; i < sl.reqs.size(); ++i) {
+    if (sl.reqs[i].result_out) {
+      *sl.reqs[i].result_out = sl.out[i];
+      --S.outstanding;
+    } else {
+      S.results.push_back(sl.out[i]);
+    }
+  }
+  S.completed += (long long)sl.reqs.size();
+  S.cv.notify_all();
+}
+
 void finish_batch(Server& S, Slot& sl, long long t_done) {
   const SlotLayout& L = S.L;
   const int32_t* npk = (const int32_t*)(sl.h + L.h_npeaks);
@@ -233,14 +298,14 @@ void finish_batch(Server& S, Slot& sl, long long t_done) {
   const hough_peak* dense = (const hough_peak*)(sl.h + L.h_dense);
   const int32_t flags = *(const int32_t*)(sl.h + L.h_status);  // device flags of the whole micro-batch
   int64_t hit0 = 0;
-  std::vector<hough_serve_result> out(sl.reqs.size());
+  sl.out.resize(sl.reqs.size());  // within the capacity reserved at open
   for (size_t i = 0; i < sl.reqs.size(); ++i) {
     const Request& r = sl.reqs[i];
     if (r.mask_out && r.n_hits) std::memcpy(r.mask_out, mask + hit0, (size_t)r.n_hits);
     const int64_t np = poff[i + 1] - poff[i];
     if (r.peaks_out && np) std::memcpy(r.peaks_out, dense + poff[i], sizeof(hough_peak) * (size_t)np);
     hit0 += r.n_hits;
-    hough_serve_result& o = out[i];
+    hough_serve_result& o = sl.out[i];
     o.id = r.id;
     o.status = flags;
     o.npeaks = npk[i];
@@ -249,29 +314,23 @@ void finish_batch(Server& S, Slot& sl, long long t_done) {
     o.t_arrival_ns = r.t_arrival;
     o.t_done_ns = t_done;
   }
-  std::lock_guard<std::mutex> lk(S.mu);
-  for (auto& o : out) S.results.push_back(o);
-  S.completed += (long long)out.size();
-  S.cv.notify_all();
+  deliver(S, sl);
 }
 
 // Requests of a batch that produced no results (flag: HOUGH_F_TIMEOUT or HOUGH_F_LAUNCH_FAILED):
 // they finish with that status and nothing is copied to their output buffers.
 void fail_batch(Server& S, Slot& sl, long long t_done, int32_t flag) {
-  std::vector<hough_serve_result> out(sl.reqs.size());
+  sl.out.resize(sl.reqs.size());
   for (size_t i = 0; i < sl.reqs.size(); ++i) {
-    hough_serve_result& o = out[i];
+    hough_serve_result& o = sl.out[i];
     std::memset(&o, 0, sizeof(o));
     o.id = sl.reqs[i].id;
     o.status = flag;
     o.t_arrival_ns = sl.reqs[i].t_arrival;
     o.t_done_ns = t_done;
   }
+  deliver(S, sl);
   sl.reqs.clear();
-  std::lock_guard<std::mutex> lk(S.mu);
-  for (auto& o : out) S.results.push_back(o);
-  S.completed += (long long)out.size();
-  S.cv.notify_all();
 }
 
 // Waits (bounded) until the slot's stream has no work left: true if it drained.
@@ -443,6 +502,9 @@ int hough_serve_open(const hough_serve_config* c, void* d_buf, size_t d_bytes, v
     return HOUGH_EWORKSPACE;
   }
   S->cfg = *c;
+  // every buffer of the serving path is allocated and touched now, none later
+  S->pending = Ring<Request>((size_t)c->queue_capacity);
+  S->results = Ring<hough_serve_result>((size_t)c->queue_capacity + (size_t)c->slots * (size_t)c->max_batch_events);
   host_trig(c->params.n_theta, &S->trig);
   cudaGetDevice(&S->device);
   if (fused_max_ctas_per_sm(S->plan) < 1) {  // also sets the kernel's shared-memory limit
@@ -452,6 +514,8 @@ int hough_serve_open(const hough_serve_config* c, void* d_buf, size_t d_bytes, v
   S->slots.resize((size_t)c->slots);
   for (int i = 0; i < c->slots; ++i) {
     Slot& sl = S->slots[i];
+    sl.reqs.reserve((size_t)c->max_batch_events);
+    sl.out.reserve((size_t)c->max_batch_events);
     sl.d = (char*)d_buf + (size_t)i * S->L.d_total;
     sl.h = (char*)h_pinned + (size_t)i * S->L.h_total;
     void* mapped = nullptr;
@@ -478,13 +542,16 @@ int hough_serve_open(const hough_serve_config* c, void* d_buf, size_t d_bytes, v
 }
 
 static int submit_at(Server* S, const int32_t* h_xy, int64_t n_hits, int64_t id, uint8_t* h_mask_out,
-                     hough_peak* h_peaks_out, long long t_arrival) {
+                     hough_peak* h_peaks_out, hough_serve_result* h_result_out, long long t_arrival) {
   if (n_hits < 0 || (n_hits > 0 && !h_xy)) return HOUGH_EINVAL;
   if (n_hits > S->cfg.max_batch_hits || n_hits > HOUGH_MAX_EVENT_HITS) return HOUGH_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
-  if ((int64_t)S->pending.size() >= S->cfg.queue_capacity) return HOUGH_EFULL;
-  S->pending.push_back(Request{h_xy, n_hits, id, h_mask_out, h_peaks_out, t_arrival});
+  // admitted only with room for the request in the queue and for its result in the ring
+  if ((int64_t)S->pending.size() >= S->cfg.queue_capacity || S->outstanding >= (long long)S->results.capacity())
+    return HOUGH_EFULL;
+  S->pending.push_back(Request{h_xy, n_hits, id, h_mask_out, h_peaks_out, h_result_out, t_arrival});
   S->pending_hits += n_hits;
+  ++S->outstanding;
   ++S->submitted;
   return HOUGH_OK;
 }
@@ -494,7 +561,7 @@ int hough_serve_submit(void* server, const int32_t* h_xy, int64_t n_hits, int64_
   if (!server) return HOUGH_EINVAL;
   Server* S = (Server*)server;
   if (S->error.load()) return S->error.load();
-  return submit_at(S, h_xy, n_hits, id, h_mask_out, h_peaks_out, now_ns());
+  return submit_at(S, h_xy, n_hits, id, h_mask_out, h_peaks_out, nullptr, now_ns());
 }
 
 int hough_serve_poll(void* server, hough_serve_result* out, int32_t max_results, int32_t* n_out) {
@@ -505,6 +572,7 @@ int hough_serve_poll(void* server, hough_serve_result* out, int32_t max_results,
   while (n < max_results && !S->results.empty()) {
     out[n++] = S->results.front();
     S->results.pop_front();
+    --S->outstanding;
   }
   *n_out = n;
   return S->error.load();
@@ -539,7 +607,7 @@ int hough_serve_close(void* server) {
 
 int hough_serve_replay(void* server, const int32_t* h_xy_pool, const int64_t* h_off_pool, int64_t pool_events,
                        const int64_t* arrival_ns, int64_t n_requests, int64_t* t_start_ns, uint8_t* h_mask_out,
-                       hough_peak* h_peaks_out) {
+                       hough_peak* h_peaks_out, hough_serve_result* h_results_out) {
   if (!server || !h_off_pool || pool_events < 1 || !arrival_ns || n_requests < 0) return HOUGH_EINVAL;
   Server* S = (Server*)server;
   const long long t0 = now_ns();
@@ -559,7 +627,8 @@ int hough_serve_replay(void* server, const int32_t* h_xy_pool, const int64_t* h_
     m += nh;
     // admission is refused while the queue is full; retry (for at most 10 s) keeping the
     // scheduled arrival time, so the wait shows up in the latency
-    while ((rc = submit_at(S, h_xy_pool + 2 * h_off_pool[e], nh, i, mo, po, due)) == HOUGH_EFULL) {
+    hough_serve_result* ro = h_results_out ? h_results_out + i : nullptr;
+    while ((rc = submit_at(S, h_xy_pool + 2 * h_off_pool[e], nh, i, mo, po, ro, due)) == HOUGH_EFULL) {
       if (now_ns() - due > 10000000000LL) {
         rc = HOUGH_ETIMEDOUT;
         break;
@@ -581,14 +650,18 @@ int hough_serve_trace(void* server, hough_serve_stats* out, hough_serve_batch_re
   out->passes = S->passes;
   out->batches = S->batches;
   out->stall_ns = kStallNs;
-  out->loop_stalls = S->loop_watch.stalls;
-  out->loop_max_gap_ns = S->loop_watch.max_gap;
-  out->loop_max_gap_at = S->loop_watch.max_at;
-  out->loop_max_gap_cpu_ns = S->loop_watch.max_cpu;
-  out->submit_stalls = S->submit_watch.stalls;
-  out->submit_max_late_ns = S->submit_watch.max_gap;
-  out->submit_max_late_at = S->submit_watch.max_at;
-  out->submit_max_late_cpu_ns = S->submit_watch.max_cpu;
+  auto put = [](const StallWatch& w, hough_serve_stall* o) {
+    o->count = w.stalls;
+    o->max_gap_ns = w.max_gap;
+    o->max_gap_at = w.max_at;
+    o->user_ns = w.max_use.user_ns;
+    o->sys_ns = w.max_use.sys_ns;
+    o->minor_faults = w.max_use.minflt;
+    o->voluntary_switches = w.max_use.nvcsw;
+    o->involuntary_switches = w.max_use.nivcsw;
+  };
+  put(S->loop_watch, &out->loop);
+  put(S->submit_watch, &out->submit);
   const long long avail = S->ring_next < HOUGH_SERVE_RECORDS ? S->ring_next : HOUGH_SERVE_RECORDS;
   const long long n = avail < max_records ? avail : max_records;
   for (long long i = 0; i < n; ++i) records[i] = record_at(*S, S->ring_next - n + i);

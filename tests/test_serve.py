@@ -154,6 +154,26 @@ def test_replayed_poisson_stream_matches_oracle(h):
     assert stats["passes"] > 0 and stats["stall_ns"] == 1_000_000
 
 
+def test_replay_results_into_caller_array(h):
+    """With a result array, the replay's requests deliver their records there (by request id),
+    nothing reaches poll(), and the counts equal the oracle's for every request."""
+    cfg = gen.CONFIGS["served"]
+    pool = gen.generate(cfg, 500, with_truth=False)
+    p = cfg_params(h, cfg)
+    ref = oracle_ref(cfg, pool)
+    n = 2500
+    arrival = np.cumsum(np.random.default_rng(3).exponential(1e9 / 200_000, size=n)).astype(np.int64)
+    res = h.Server.result_array(n)
+    with h.Server(p, slots=4, max_batch_events=64, flush_us=50, queue_capacity=256) as srv:
+        srv.replay(pool.xy, pool.off, arrival, results_out=res)
+        srv.drain(60)
+        assert len(srv.poll()) == 0
+    ev_of = np.arange(n) % pool.n_events
+    assert np.array_equal(res["id"], np.arange(n)) and np.all(res["status"] == 0)
+    assert np.array_equal(res["npeaks"], ref.npeaks[ev_of]) and np.array_equal(res["nkept"], ref.nkept[ev_of])
+    assert np.all(res["t_done_ns"] > res["t_arrival_ns"])
+
+
 def test_failed_launch_reports_no_result_as_ok(h):
     """A micro-batch whose launch fails (a host-side injected CUDA error, before anything is
     enqueued) finishes its requests with F_LAUNCH_FAILED, zero counts and untouched output
