@@ -644,9 +644,12 @@ def main():
     for _ in range(2):  # graphs, streams and host pages warm
         runner(xy_h, off_h, stream)
     barrier()
+    call_ms = []
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
+        t1 = time.perf_counter()
         runner(xy_h, off_h, stream)
+        call_ms.append(1e3 * (time.perf_counter() - t1))
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = n_events * ws * args.e2e_steps / e2e_s
@@ -730,7 +733,7 @@ def main():
         "latency": {"batch_ms": ms_step, "note": "every event of the batch completes within one step"},
         "served": served,
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "stages_ms": e2e_stages},
+                "stages_ms": e2e_stages, "calls_ms": [round(x, 2) for x in call_ms]},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "smem_atomic", "kernel": "fused_kernel (persistent)",
                      "achieved": votes_per_s / 1e9, "peak": lane / 1e9, "unit": "Gvotes/s",

@@ -114,8 +114,9 @@ static bool layout(Plan& pl) {
   {
     int iter_words = 0;
     if (it_whole) {
-      // candidate keys, then 2 state bits a cell (also room for the walk's 1-bit bitmap)
-      const int cand_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 15) / 16;
+      // candidate keys, then 2 state bits a cell (also room for the walk's 1-bit bitmap), then
+      // two lists of undecided candidates (16-bit indices)
+      const int cand_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 15) / 16 + pl.iter_act;
       iter_words = iter_scratch_words(pl.n_theta, pl.n_rho, kIterSliceRows);
       if (pl.iter_cap > 0 && cand_words > iter_words) iter_words = cand_words;
     }
@@ -313,7 +314,10 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       const int icap0 = pl.peak_mode == HOUGH_PEAK_ITERATIVE && T == 1 ? 8192 : 0;
       for (int icap = icap0; icap >= 0; icap = icap > 1024 ? icap / 2 : icap - 1024) {
         pl.iter_cap = icap;
-        if (layout(pl)) return HOUGH_OK;
+        for (int act = icap > 0 ? 2048 : 0; act >= 0; act = act > 256 ? act / 2 : act - 256) {
+          pl.iter_act = act;
+          if (layout(pl)) return HOUGH_OK;
+        }
       }
     }
     if (p->theta_tiles) return HOUGH_ESMEM;

@@ -429,14 +429,15 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
 // cell was kept), and one with no undecided higher-ranked cell in its window is kept. Decisions
 // are final, and each round decides at least the highest-ranked undecided candidate; states
 // read while others change are either the old or the final one, which only speeds this up.
-// The kept keys are then gathered into st (as many as its st_words hold) and sorted. Returns
+// The kept keys are then gathered into st (as many as its st_words hold) and ordered by rank (by
+// counting the kept keys above each, up to 1,024 of them; else bitonic). Returns
 // the count, or -1 (written nothing) past 64 rounds or st_words, or with more than 64
 // candidates a thread. s[2] .. s[5] used.
 template <class Cells>
 __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int maxp, const uint32_t* keys, int C,
-                              uint32_t* st, int st_words, hough_peak* dst, int* s) {
+                              uint32_t* st, int st_words, uint16_t* act, int act_cap, hough_peak* dst, int* s) {
   const int lane = threadIdx.x & 31, bd = blockDim.x;
-  if (C > 64 * bd) return -1;
+  if (C > 64 * bd || C > 65536) return -1;
   const int nst = (NT * NR + 15) >> 4;
   for (int i = threadIdx.x; i < nst; i += bd) st[i] = 0u;
   if (threadIdx.x < 4) s[2 + threadIdx.x] = 0;
@@ -447,10 +448,18 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     atomicOr(&st[c >> 4], 1u << ((c & 15) << 1));
   }
   __syncthreads();
+  // Once at most act_cap candidates are undecided, a round visits only those: the previous
+  // round listed them (two lists of act_cap 16-bit indices, alternating), so its time is about
+  // one window scan instead of the scans of the thread holding the most undecided candidates.
+  bool listed = false;  // uniform
   for (int round = 0;; ++round) {
     if (round == 64) return -1;  // uniform
-    int und = 0;
-    for (int i = threadIdx.x; i < C; i += bd) {
+    const int r3 = round % 3;
+    const uint16_t* cur = act + (round & 1) * act_cap;
+    uint16_t* nxt = act + ((round + 1) & 1) * act_cap;
+    const int n_cur = listed ? s[2 + (round + 2) % 3] : C;  // the previous round's undecided
+    for (int t = threadIdx.x; t < n_cur; t += bd) {
+      const int i = listed ? (int)cur[t] : t;
       const uint32_t key = keys[i];
       const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int c = j * NR + k;
@@ -486,17 +495,21 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
           }
         }
       }
-      if (drop) atomicXor(&st[c >> 4], 3u << ((c & 15) << 1));  // 1 -> 2
-      else if (all) atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
-      else ++und;
+      if (drop) {
+        atomicXor(&st[c >> 4], 3u << ((c & 15) << 1));  // 1 -> 2
+      } else if (all) {
+        atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+      } else {  // counted, and listed for the next round while the list has room
+        const int pos = atomicAdd(&s[2 + r3], 1);
+        if (pos < act_cap) nxt[pos] = (uint16_t)i;
+      }
     }
     // undecided count: three rotating counters, so that one barrier a round suffices
-    const int r3 = round % 3;
-    und = __reduce_add_sync(0xffffffffu, und);
-    if (lane == 0 && und) atomicAdd(&s[2 + r3], und);
     if (threadIdx.x == 0) s[2 + (r3 + 1) % 3] = 0;
     __syncthreads();
-    if (s[2 + r3] == 0) break;
+    const int und = s[2 + r3];
+    if (und == 0) break;
+    listed = und <= act_cap;
   }
   HOUGH_PHASE(HOUGH_PHASE_IT_RESOLVE);
   // the kept keys, gathered into st once every state has been read
@@ -525,10 +538,20 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       if ((flags >> t) & 1ull) st[atomicAdd(&s[4], 1)] = keys[i];
     }
   }
-  for (int i = nk + threadIdx.x; i < N; i += bd) st[i] = 0u;
   __syncthreads();
-  bitonic_desc(st, N);
-  for (int i = threadIdx.x; i < min(nk, maxp); i += bd) store_peak(dst + i, st[i]);
+  if (nk <= 1024) {  // a kept key's rank is the count of kept keys above it (keys are distinct)
+    for (int i = threadIdx.x; i < nk; i += bd) {
+      const uint32_t key = st[i];
+      int r = 0;
+      for (int m = 0; m < nk; ++m) r += st[m] > key;
+      if (r < maxp) store_peak(dst + r, key);
+    }
+  } else {
+    for (int i = nk + threadIdx.x; i < N; i += bd) st[i] = 0u;
+    __syncthreads();
+    bitonic_desc(st, N);
+    for (int i = threadIdx.x; i < min(nk, maxp); i += bd) store_peak(dst + i, st[i]);
+  }
   __syncthreads();
   HOUGH_PHASE(HOUGH_PHASE_IT_ORDER);
   return nk;
@@ -610,13 +633,14 @@ __device__ inline int resolve_walk(int NT, int NR, int R, int maxp, uint32_t* ke
 template <class Cells>
 __device__ int extract_iterative(Cells& cells, int NT, int NR, int SH, int thr, int rel_num, int rel_den, int R,
                                  int maxp, uint32_t* scratch, int cap, uint32_t* sup, int st_words,
-                                 hough_peak* dst, int* s) {
+                                 hough_peak* dst, int* s, uint16_t* act = nullptr, int act_cap = 0) {
   if (cap > 0) {
     int tq = 0;
     const int C = collect_candidates(cells, NT, NR, thr, rel_num, rel_den, scratch, cap, s, &tq);
     if (C >= 0) {
       if (st_words > 0) {
-        const int n = resolve_rounds(cells, NT, NR, R, tq, maxp, scratch, C, scratch + cap, st_words, dst, s);
+        const int n =
+            resolve_rounds(cells, NT, NR, R, tq, maxp, scratch, C, scratch + cap, st_words, act, act_cap, dst, s);
         if (n >= 0) return n;
       }
       return resolve_walk(NT, NR, R, maxp, scratch, C, sup ? sup : scratch + cap, dst, s);

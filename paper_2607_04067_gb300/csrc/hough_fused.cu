@@ -1269,6 +1269,25 @@ struct SparseCands {
   int C;
 };
 
+// Votes of a cell that is a candidate of a sparse list (the dense rounds only ask for candidates):
+// the row within its column's list by binary search.
+struct ListCells {
+  static constexpr bool kPairs = false;
+  const uint32_t* keys;
+  const int* colstart;
+  __device__ int get(int j, int k) const {
+    int lo = colstart[j];
+    const int end = colstart[j + 1];
+    int hi = end;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (1023 - (int)(keys[mid] & 1023u) < k) lo = mid + 1;
+      else hi = mid;
+    }
+    return (lo < end && 1023 - (int)(keys[lo] & 1023u) == k) ? (int)(keys[lo] >> 20) : 0;
+  }
+};
+
 // Visits every other candidate in the suppression window of candidate i (columns j - R .. j + R
 // and rows k - R .. k + R; a column past either end of the theta range is taken from the other end
 // with the rows mirrored, rows beyond the rho edges do not exist), each column's rows found by a
@@ -1510,7 +1529,20 @@ __device__ int merge_iterative(const Plan& pl, const FusedIO& io, unsigned char*
   block_exscan(colstart, NT + 1, sh.tmp);
   const SparseCands sc{keys, colstart, C};
   unsigned char* work = reinterpret_cast<unsigned char*>(keys + C);
-  return resolve_sparse(pl, sc, cap, work, (int)(smem + pl.off_unres - work), io.peaks + e * (long long)maxp, sh);
+  const int work_bytes = (int)(smem + pl.off_unres - work);
+  hough_peak* dst = io.peaks + e * (long long)maxp;
+  // the rounds on a 2-bit state per cell of the event where that map fits (512 x 512: 64 KB);
+  // the rank of an undecided neighbour comes from its key, found by binary search in its column
+  int stw = 32;
+  while (stw < ((NT * NR + 15) >> 4)) stw <<= 1;
+  if (4LL * stw <= work_bytes) {
+    ListCells lc{keys, colstart};
+    const int act_cap = (int)min(2048LL, (work_bytes - 4LL * stw) / 4);  // two lists of 16-bit indices
+    const int n = resolve_rounds(lc, NT, NR, R, 0, maxp, keys, C, reinterpret_cast<uint32_t*>(work), stw,
+                                 reinterpret_cast<uint16_t*>(work + 4LL * stw), act_cap, dst, sh.tmp);
+    if (n >= 0) return n;  // else (past 64 rounds) the sparse form, which needs only keys and colstart
+  }
+  return resolve_sparse(pl, sc, cap, work, work_bytes, dst, sh);
 }
 
 // Steps 1-2 of a work item: clears the CTA's accumulator of theta tile t (with the halo columns,
@@ -1706,9 +1738,10 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       __syncthreads();
       HOUGH_PHASE(HOUGH_PHASE_SCAN);
       HOUGH_PHASE(HOUGH_PHASE_SCAN);
+      const int st_words = (NT * NR + 15) >> 4;
       return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
-                               maxp, pbits, pl.iter_cap, nullptr, (NT * NR + 15) >> 4,
-                               io.peaks + e * (long long)maxp, sh.tmp);
+                               maxp, pbits, pl.iter_cap, nullptr, st_words, io.peaks + e * (long long)maxp, sh.tmp,
+                               reinterpret_cast<uint16_t*>(pbits + pl.iter_cap + st_words), pl.iter_act);
     };
     total = pl.mp ? iterative(FusedCells<A32, true>{acc, Wd, nrp, pl.rows_phys})
                   : iterative(FusedCells<A32, false>{acc, Wd, nrp, pl.rows_phys});

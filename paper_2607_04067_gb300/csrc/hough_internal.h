@@ -18,6 +18,7 @@ struct Plan {
   int n_theta, n_rho, threshold, keep_hw, max_peaks;
   int peak_mode, rel_num, rel_den, nms_radius;  // peak finder (0: 3x3 local maxima, 1: iterative)
   int iter_cap;   // iterative finder: candidate keys of its candidate form (0: one pass per peak only)
+  int iter_act;   // iterative finder: entries of each of its two lists of undecided candidates
   int tiles;      // theta tiles per event
   int tile_w;     // columns per tile (last tile may be narrower)
   int groups;     // 32-column groups per tile
