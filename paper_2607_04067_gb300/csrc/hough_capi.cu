@@ -314,7 +314,8 @@ int make_plan(const hough_params* p, Plan& pl, int acc32 = -1) {
       const int icap0 = pl.peak_mode == HOUGH_PEAK_ITERATIVE && T == 1 ? 8192 : 0;
       for (int icap = icap0; icap >= 0; icap = icap > 1024 ? icap / 2 : icap - 1024) {
         pl.iter_cap = icap;
-        for (int act = icap > 0 ? 2048 : 0; act >= 0; act = act > 256 ? act / 2 : act - 256) {
+        for (int act = icap > 0 ? 2048 : 0; act >= 0;
+             act = act > 1024 ? act - 512 : act > 256 ? act / 2 : act - 256) {  // 2048, 1536, 1024, 512, 256, 0
           pl.iter_act = act;
           if (layout(pl)) return HOUGH_OK;
         }

@@ -422,13 +422,15 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
 }
 
 // Stage 2, in parallel rounds (all threads): st holds 2 bits per cell (cell (j, k) is pair
-// j NR + k): 0 not a candidate, 1 undecided, 2 dropped, 3 kept; a candidate's owner thread
-// changes them with one atomic, so readers see a whole state. Each round, an undecided
-// candidate with a kept cell in its window is dropped (a kept cell in the window of an
-// undecided one always ranks above it: otherwise that one would have been dropped before the
-// cell was kept), and one with no undecided higher-ranked cell in its window is kept. Decisions
-// are final, and each round decides at least the highest-ranked undecided candidate; states
-// read while others change are either the old or the final one, which only speeds this up.
+// j NR + k): 0 not a candidate or dropped, 1 undecided, 3 kept, each changed by one atomic, so
+// readers see a whole state. Each round, an undecided candidate with no undecided higher-ranked
+// cell in its window is kept, and the keeping thread at once drops every other candidate of
+// that window (they all rank below it and none is kept: a kept one would have dropped it); one
+// with a kept cell in its window (read before that cell's drops reached it) drops itself.
+// Decisions are final, and each round keeps at least the highest-ranked undecided candidate;
+// states read while others change are either the old or the final one, which only speeds this
+// up. Pushing the drops halves the rounds against drops found by the dropped candidates' owners
+// in the next round (8.1 -> 4.2 on the batched events).
 // The kept keys are then gathered into st (as many as its st_words hold) and ordered by rank (by
 // counting the kept keys above each, up to 1,024 of them; else bitonic). Returns
 // the count, or -1 (written nothing) past 64 rounds or st_words, or with more than 64
@@ -443,6 +445,25 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
   if (threadIdx.x < 4) s[2 + threadIdx.x] = 0;
   __syncthreads();
   auto cell_of = [&](uint32_t key) { return (1023 - (int)((key >> 10) & 1023u)) * NR + 1023 - (int)(key & 1023u); };
+  // drops (1 -> 0) the candidates of column j + a of the window of the kept cell (j, k), except
+  // the cell itself; a cleared low bit leaves a 0 as it was and cannot meet a kept cell
+  auto push_column = [&](int j, int k, int a) {
+    int jj = j + a, r0 = max(0, k - R), r1 = min(NR - 1, k + R);
+    if (jj < 0 || jj >= NT) {  // across the theta wrap: the other end, rho mirrored
+      jj = jj < 0 ? jj + NT : jj - NT;
+      const int t0 = NR - 1 - r1;
+      r1 = NR - 1 - r0;
+      r0 = t0;
+    }
+    const int b0 = (jj * NR + r0) << 1, b1 = (jj * NR + r1) << 1, bc = a == 0 ? (j * NR + k) << 1 : -1;
+    for (int w = b0 >> 5; w <= (b1 >> 5); ++w) {
+      uint32_t m = 0x55555555u;
+      if (w == (b0 >> 5)) m &= 0xffffffffu << (b0 & 31);
+      if (w == (b1 >> 5)) m &= 0xffffffffu >> (31 - (b1 & 31));
+      if (w == (bc >> 5)) m &= ~(1u << (bc & 31));
+      atomicAnd(&st[w], ~m);
+    }
+  };
   for (int i = threadIdx.x; i < C; i += bd) {
     const int c = cell_of(keys[i]);
     atomicOr(&st[c >> 4], 1u << ((c & 15) << 1));
@@ -450,7 +471,8 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
   __syncthreads();
   // Once at most act_cap candidates are undecided, a round visits only those: the previous
   // round listed them (two lists of act_cap 16-bit indices, alternating), so its time is about
-  // one window scan instead of the scans of the thread holding the most undecided candidates.
+  // one window scan instead of the scans of the thread holding the most undecided candidates;
+  // once at most four a warp are left, each takes a warp.
   bool listed = false;  // uniform
   for (int round = 0;; ++round) {
     if (round == 64) return -1;  // uniform
@@ -458,50 +480,105 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     const uint16_t* cur = act + (round & 1) * act_cap;
     uint16_t* nxt = act + ((round + 1) & 1) * act_cap;
     const int n_cur = listed ? s[2 + (round + 2) % 3] : C;  // the previous round's undecided
-    for (int t = threadIdx.x; t < n_cur; t += bd) {
-      const int i = listed ? (int)cur[t] : t;
+    if (listed && n_cur <= 4 * (bd >> 5) && R <= 7) {
+      // Few left: a warp per undecided candidate, its lanes on the cells of the window, so that a
+      // round costs one state read and at most one vote read per lane instead of one thread's walk
+      // over the window's columns.
+      const int W = 2 * R + 1, nc = W * W;
+      const uint32_t mW = ((1u << 21) + W - 1) / W;  // q / W = (q mW) >> 21, exact for q < 2^10
+      for (int t = threadIdx.x >> 5; t < n_cur; t += bd >> 5) {
+        const int i = (int)cur[t];
+        const uint32_t key = keys[i];
+        const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+        const int c = j * NR + k;
+        const uint32_t sw = __shfl_sync(0xffffffffu, st[c >> 4], 0);  // one reading for the warp
+        if (((sw >> ((c & 15) << 1)) & 3u) != 1u) continue;  // dropped since it was listed
+        bool kept_seen = false, above = false;
+        for (int q = lane; q < nc; q += 32) {
+          const int qa = (int)(((uint32_t)q * mW) >> 21);
+          int jj = j + qa - R, kk = k + (q - qa * W) - R;
+          if (kk < 0 || kk >= NR || (jj == j && kk == k)) continue;
+          if (jj < 0 || jj >= NT) {  // across the theta wrap: the other end, rho mirrored
+            jj = jj < 0 ? jj + NT : jj - NT;
+            kk = NR - 1 - kk;
+          }
+          const int cc = jj * NR + kk;
+          const uint32_t sv = (st[cc >> 4] >> ((cc & 15) << 1)) & 3u;
+          if (sv == 3u) {
+            kept_seen = true;
+          } else if (sv == 1u) {
+            const uint32_t kd = ((uint32_t)cells.get(jj, kk) << 20) | ((uint32_t)(1023 - jj) << 10) |
+                                (uint32_t)(1023 - kk);
+            above = above || kd > key;
+          }
+        }
+        kept_seen = __any_sync(0xffffffffu, kept_seen);
+        above = __any_sync(0xffffffffu, above);
+        if (kept_seen) {
+          if (lane == 0) atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
+        } else if (!above) {
+          if (lane == 0) atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+          if (lane < W) push_column(j, k, lane - R);
+        } else if (lane == 0) {
+          const int pos = atomicAdd(&s[2 + r3], 1);
+          if (pos < act_cap) nxt[pos] = (uint16_t)i;
+        }
+      }
+    } else
+    for (int t0 = threadIdx.x - lane; t0 < n_cur; t0 += bd) {  // slots of a warp: uniform
+      const int t = t0 + lane;
+      int jk = -1;  // a cell kept in this slot: the whole warp pushes its drops below
+      const int i = t < n_cur ? (listed ? (int)cur[t] : t) : 0;
       const uint32_t key = keys[i];
       const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int c = j * NR + k;
-      if (((st[c >> 4] >> ((c & 15) << 1)) & 3u) != 1u) continue;
-      bool drop = false, all = true;
-      const int k0 = max(0, k - R), k1 = min(NR - 1, k + R);
-      for (int a = -R; a <= R && !drop; ++a) {
-        int jj = j + a, r0 = k0, r1 = k1;
-        if (jj < 0 || jj >= NT) {
-          jj = jj < 0 ? jj + NT : jj - NT;
-          r0 = NR - 1 - k1;
-          r1 = NR - 1 - k0;
+      if (t < n_cur && ((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
+        bool drop = false, all = true;
+        const int k0 = max(0, k - R), k1 = min(NR - 1, k + R);
+        // round 0 starts with nothing kept, so there it stops at the first higher-ranked cell (a cell
+        // kept meanwhile with it in its window drops it)
+        for (int a = -R; a <= R && !drop && (all || round > 0); ++a) {
+          int jj = j + a, r0 = k0, r1 = k1;
+          if (jj < 0 || jj >= NT) {
+            jj = jj < 0 ? jj + NT : jj - NT;
+            r0 = NR - 1 - k1;
+            r1 = NR - 1 - k0;
+          }
+          // the states of rows r0 .. r1 of column jj, 16 cells at a time
+          const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
+          for (int off = 0; off < nb && !drop; off += 32) {
+            const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
+            uint32_t f = st[w] >> sh;
+            if (sh && sh + len > 32) f |= st[w + 1] << (32 - sh);
+            if (len < 32) f &= (1u << len) - 1u;
+            if ((f & (f >> 1)) & 0x55555555u) {  // a kept cell
+              drop = true;
+              break;
+            }
+            uint32_t m = f & ~(f >> 1) & 0x55555555u;  // undecided cells
+            while (m && all) {
+              const int t = __ffs(m) - 1;
+              const int kr = r0 + ((off + t) >> 1);
+              const uint32_t kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) |
+                                  (uint32_t)(1023 - kr);
+              if (kd > key) all = false;  // an undecided cell ranked above (the cell itself is equal)
+              m &= m - 1u;
+            }
+          }
         }
-        // the states of rows r0 .. r1 of column jj, 16 cells at a time
-        const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
-        for (int off = 0; off < nb && !drop; off += 32) {
-          const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
-          uint32_t f = st[w] >> sh;
-          if (sh && sh + len > 32) f |= st[w + 1] << (32 - sh);
-          if (len < 32) f &= (1u << len) - 1u;
-          if ((f & (f >> 1)) & 0x55555555u) {  // a kept cell
-            drop = true;
-            break;
-          }
-          uint32_t m = f & ~(f >> 1) & 0x55555555u;  // undecided cells
-          while (m && all) {
-            const int t = __ffs(m) - 1;
-            const int kr = r0 + ((off + t) >> 1);
-            const uint32_t kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) |
-                                (uint32_t)(1023 - kr);
-            if (kd > key) all = false;  // an undecided cell ranked above (the cell itself is equal)
-            m &= m - 1u;
-          }
+        if (drop) {
+          atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
+        } else if (all) {
+          atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+          jk = (j << 16) | k;
+        } else {  // counted, and listed for the next round while the list has room
+          const int pos = atomicAdd(&s[2 + r3], 1);
+          if (pos < act_cap) nxt[pos] = (uint16_t)i;
         }
       }
-      if (drop) {
-        atomicXor(&st[c >> 4], 3u << ((c & 15) << 1));  // 1 -> 2
-      } else if (all) {
-        atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
-      } else {  // counted, and listed for the next round while the list has room
-        const int pos = atomicAdd(&s[2 + r3], 1);
-        if (pos < act_cap) nxt[pos] = (uint16_t)i;
+      for (unsigned kb = __ballot_sync(0xffffffffu, jk >= 0); kb; kb &= kb - 1u) {
+        const int x = __shfl_sync(0xffffffffu, jk, __ffs(kb) - 1);
+        for (int a = lane - R; a <= R; a += 32) push_column(x >> 16, x & 0xffff, a);
       }
     }
     // undecided count: three rotating counters, so that one barrier a round suffices

@@ -543,12 +543,15 @@ def test_iterative_matches_greedy_restatement(seed):
     assert [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk] == exp
 
 
-def _rounds_peaks(acc, T, num, den, R):
+def _rounds_peaks(acc, T, num, den, R, push=False, order_rng=None):
     """The kept set reached by rounds of local rules (no ordering of the work): a candidate
     (cell passing the thresholds) is dropped once a kept candidate lies in its window, and kept
     once every higher-ranked candidate in its window is dropped; rank is (votes desc, raster
     asc). Each round applies the rules to every undecided candidate on the states of the round
-    before. The kept cells, listed in rank order."""
+    before. With push, a candidate kept in a round also drops every undecided candidate of its
+    window at once. With order_rng, a round visits the candidates in a random order and each
+    decision (and push) is seen by the visits after it (the GPU's threads read states while
+    others change them). The kept cells, listed in rank order."""
     NT, NR = acc.shape
     amax = int(acc.max()) if acc.size else 0
     cand = [(j, k) for j in range(NT) for k in range(NR) if acc[j, k] >= T and int(acc[j, k]) * den >= num * amax]
@@ -557,13 +560,20 @@ def _rounds_peaks(acc, T, num, den, R):
     state = {c: 0 for c in cand}  # 0 undecided, 1 dropped, 2 kept
     for _ in range(len(cand) + 1):
         new = dict(state)
-        for c in cand:
-            if state[c]:
+        seen = new if order_rng is not None else state  # in place: later visits see earlier ones
+        visit = list(cand) if order_rng is None else [cand[i] for i in order_rng.permutation(len(cand))]
+        for c in visit:
+            if seen[c]:
                 continue
-            if any(state[d] == 2 for d in window[c]):
+            if any(seen[d] == 2 for d in window[c]):
                 new[c] = 1
-            elif all(state[d] == 1 for d in window[c] if rank[d] < rank[c]):
+            elif all(seen[d] == 1 for d in window[c] if rank[d] < rank[c]):
                 new[c] = 2
+                if push:
+                    for d in window[c]:
+                        assert new[d] != 2, "a kept cell never lies in the window of one kept later"
+                        if new[d] == 0:
+                            new[d] = 1
         if new == state:
             break
         state = new
@@ -589,9 +599,13 @@ def test_iterative_local_rules_reach_the_greedy_list(seed):
             assert _in_window(a, b, R, NT, NR) == _in_window(b, a, R, NT, NR)
     p = oracle.params(NT, NR, T, 1, 1000, peak_mode=oracle.PEAK_ITERATIVE, rel_num=num, rel_den=den, nms_radius=R)
     n, pk = oracle.peaks_iterative(acc, p)
-    got = _rounds_peaks(acc, T, num, den, R)
-    assert n == len(got)
-    assert [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk] == got
+    exp = [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk]
+    # synchronous rounds, with and without pushed drops, and in-place rounds in random orders
+    for push, order in ((False, None), (True, None), (True, np.random.default_rng(seed)),
+                        (False, np.random.default_rng(50 + seed))):
+        got = _rounds_peaks(acc, T, num, den, R, push=push, order_rng=order)
+        assert n == len(got)
+        assert exp == got, (push, order is not None)
 
 
 def test_iterative_hand_cases():
