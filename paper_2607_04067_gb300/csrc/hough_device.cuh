@@ -469,12 +469,117 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     atomicOr(&st[c >> 4], 1u << ((c & 15) << 1));
   }
   __syncthreads();
-  // Once at most act_cap candidates are undecided, a round visits only those: the previous
-  // round listed them (two lists of act_cap 16-bit indices, alternating), so its time is about
-  // one window scan instead of the scans of the thread holding the most undecided candidates;
-  // once at most four a warp are left, each takes a warp.
-  bool listed = false;  // uniform
-  for (int round = 0;; ++round) {
+  // The decision on undecided candidate (j, k) from the states of its window: 1 (drop) for a kept
+  // cell in it, 2 (keep) for no undecided higher-ranked cell in it, else 0. The scan stops at the
+  // first higher-ranked undecided cell: a kept cell it then misses drops the candidate by its push.
+  auto decide = [&](int j, int k, uint32_t key) -> int {
+    bool drop = false, all = true;
+    const int k0 = max(0, k - R), k1 = min(NR - 1, k + R);
+    for (int a = -R; a <= R && !drop && all; ++a) {
+      int jj = j + a, r0 = k0, r1 = k1;
+      if (jj < 0 || jj >= NT) {
+        jj = jj < 0 ? jj + NT : jj - NT;
+        r0 = NR - 1 - k1;
+        r1 = NR - 1 - k0;
+      }
+      // the states of rows r0 .. r1 of column jj, 16 cells at a time
+      const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
+      for (int off = 0; off < nb && !drop && all; off += 32) {
+        const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
+        uint32_t f = st[w] >> sh;
+        if (sh && sh + len > 32) f |= st[w + 1] << (32 - sh);
+        if (len < 32) f &= (1u << len) - 1u;
+        if ((f & (f >> 1)) & 0x55555555u) {  // a kept cell
+          drop = true;
+          break;
+        }
+        uint32_t m = f & ~(f >> 1) & 0x55555555u;  // undecided cells
+        while (m && all) {
+          const int kr = r0 + ((off + __ffs(m) - 1) >> 1);
+          const uint32_t kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) |
+                              (uint32_t)(1023 - kr);
+          if (kd > key) all = false;  // an undecided cell ranked above (the cell itself is equal)
+          m &= m - 1u;
+        }
+      }
+    }
+    return drop ? 1 : all ? 2 : 0;
+  };
+  // Candidates kept in a slot of a warp (jk = j << 16 | k, else -1): the warp pushes their drops.
+  auto push_slot = [&](int jk) {
+    for (unsigned kb = __ballot_sync(0xffffffffu, jk >= 0); kb; kb &= kb - 1u) {
+      const int x = __shfl_sync(0xffffffffu, jk, __ffs(kb) - 1);
+      for (int a = lane - R; a <= R; a += 32) push_column(x >> 16, x & 0xffff, a);
+    }
+  };
+  // Round 0 in three passes, since most candidates are not local maxima and a warp's scans last
+  // as long as its slowest lane's. (1) A candidate with a higher-ranked cell among its eight
+  // neighbours (votes alone decide: cells below the threshold rank below every candidate) stays
+  // undecided; the others are listed. (2) The listed ones are decided on their windows, a kept one
+  // pushing its drops. (3) The candidates still undecided are listed for round 1. Lists: act (the
+  // survivors), then act + act_cap (round 1's); s[4] counts the survivors, s[2] the undecided.
+  {
+    for (int t0 = threadIdx.x - lane; t0 < C; t0 += bd) {  // slots of a warp: uniform
+      const int t = t0 + lane;
+      bool sv = t < C;
+      if (sv && R > 0) {
+        const uint32_t key = keys[t];
+        const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          int jj = j + q / 3 - 1, kk = k + q % 3 - 1;
+          if (q == 4 || kk < 0 || kk >= NR) continue;
+          if (jj < 0 || jj >= NT) {  // across the theta wrap: the other end, rho mirrored
+            jj = jj < 0 ? jj + NT : jj - NT;
+            kk = NR - 1 - kk;
+          }
+          const uint32_t kd = ((uint32_t)cells.get(jj, kk) << 20) | ((uint32_t)(1023 - jj) << 10) |
+                              (uint32_t)(1023 - kk);
+          sv = sv && kd <= key;
+        }
+      }
+      if (sv) {
+        const int pos = atomicAdd(&s[4], 1);
+        if (pos < act_cap) act[pos] = (uint16_t)t;
+      }
+    }
+    __syncthreads();
+    const int ns = s[4], n = ns <= act_cap ? ns : C;  // past the list's room: every candidate
+    for (int t0 = threadIdx.x - lane; t0 < n; t0 += bd) {
+      const int t = t0 + lane;
+      const int i = t < n ? (ns <= act_cap ? (int)act[t] : t) : 0;
+      const uint32_t key = keys[i];
+      const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+      const int c = j * NR + k;
+      int jk = -1;
+      if (t < n && ((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
+        const int d = decide(j, k, key);
+        if (d == 1) {
+          atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
+        } else if (d == 2) {
+          atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+          jk = (j << 16) | k;
+        }
+      }
+      push_slot(jk);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < C; i += bd) {
+      const int c = cell_of(keys[i]);
+      if (((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
+        const int pos = atomicAdd(&s[2], 1);
+        if (pos < act_cap) act[act_cap + pos] = (uint16_t)i;
+      }
+    }
+    __syncthreads();
+  }
+  // Rounds 1, 2, ...: once at most act_cap candidates are undecided, a round visits only those:
+  // the round before listed them (two lists of act_cap 16-bit indices, alternating), so its time
+  // is about one window scan instead of the scans of the thread holding the most undecided
+  // candidates; once at most four a warp are left, each takes a warp.
+  bool listed = s[2] <= act_cap;  // uniform
+  if (s[2] > 0)
+  for (int round = 1;; ++round) {
     if (round == 64) return -1;  // uniform
     const int r3 = round % 3;
     const uint16_t* cur = act + (round & 1) * act_cap;
@@ -527,48 +632,16 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     } else
     for (int t0 = threadIdx.x - lane; t0 < n_cur; t0 += bd) {  // slots of a warp: uniform
       const int t = t0 + lane;
-      int jk = -1;  // a cell kept in this slot: the whole warp pushes its drops below
       const int i = t < n_cur ? (listed ? (int)cur[t] : t) : 0;
       const uint32_t key = keys[i];
       const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int c = j * NR + k;
+      int jk = -1;
       if (t < n_cur && ((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
-        bool drop = false, all = true;
-        const int k0 = max(0, k - R), k1 = min(NR - 1, k + R);
-        // round 0 starts with nothing kept, so there it stops at the first higher-ranked cell (a cell
-        // kept meanwhile with it in its window drops it)
-        for (int a = -R; a <= R && !drop && (all || round > 0); ++a) {
-          int jj = j + a, r0 = k0, r1 = k1;
-          if (jj < 0 || jj >= NT) {
-            jj = jj < 0 ? jj + NT : jj - NT;
-            r0 = NR - 1 - k1;
-            r1 = NR - 1 - k0;
-          }
-          // the states of rows r0 .. r1 of column jj, 16 cells at a time
-          const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
-          for (int off = 0; off < nb && !drop; off += 32) {
-            const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
-            uint32_t f = st[w] >> sh;
-            if (sh && sh + len > 32) f |= st[w + 1] << (32 - sh);
-            if (len < 32) f &= (1u << len) - 1u;
-            if ((f & (f >> 1)) & 0x55555555u) {  // a kept cell
-              drop = true;
-              break;
-            }
-            uint32_t m = f & ~(f >> 1) & 0x55555555u;  // undecided cells
-            while (m && all) {
-              const int t = __ffs(m) - 1;
-              const int kr = r0 + ((off + t) >> 1);
-              const uint32_t kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) |
-                                  (uint32_t)(1023 - kr);
-              if (kd > key) all = false;  // an undecided cell ranked above (the cell itself is equal)
-              m &= m - 1u;
-            }
-          }
-        }
-        if (drop) {
+        const int d = decide(j, k, key);
+        if (d == 1) {
           atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
-        } else if (all) {
+        } else if (d == 2) {
           atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
           jk = (j << 16) | k;
         } else {  // counted, and listed for the next round while the list has room
@@ -576,10 +649,7 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
           if (pos < act_cap) nxt[pos] = (uint16_t)i;
         }
       }
-      for (unsigned kb = __ballot_sync(0xffffffffu, jk >= 0); kb; kb &= kb - 1u) {
-        const int x = __shfl_sync(0xffffffffu, jk, __ffs(kb) - 1);
-        for (int a = lane - R; a <= R; a += 32) push_column(x >> 16, x & 0xffff, a);
-      }
+      push_slot(jk);
     }
     // undecided count: three rotating counters, so that one barrier a round suffices
     if (threadIdx.x == 0) s[2 + (r3 + 1) % 3] = 0;
