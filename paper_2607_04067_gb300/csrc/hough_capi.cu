@@ -116,7 +116,7 @@ static bool layout(Plan& pl) {
     if (it_whole) {
       // candidate keys, then 2 state bits a cell (also room for the walk's 1-bit bitmap), then
       // two lists of undecided candidates (16-bit indices)
-      const int cand_words = pl.iter_cap + (pl.n_theta * pl.n_rho + 15) / 16 + pl.iter_act;
+      const int cand_words = pl.iter_cap + (((pl.n_theta * pl.n_rho + 15) / 16 + 31) & ~31) + pl.iter_act;
       iter_words = iter_scratch_words(pl.n_theta, pl.n_rho, kIterSliceRows);
       if (pl.iter_cap > 0 && cand_words > iter_words) iter_words = cand_words;
     }

@@ -421,6 +421,17 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
   return C > cap ? -1 : C;
 }
 
+// Position of this lane's entry in a shared list counted by *cnt (-1 when p is false), one
+// atomic a warp; every lane of the warp calls it.
+__device__ __forceinline__ int warp_append(int* cnt, bool p) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(0xffffffffu, p);
+  int base = 0;
+  if (lane == 0 && b) base = atomicAdd(cnt, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return p ? base + __popc(b & ((1u << lane) - 1u)) : -1;
+}
+
 // Stage 2, in parallel rounds (all threads): st holds 2 bits per cell (cell (j, k) is pair
 // j NR + k): 0 not a candidate or dropped, 1 undecided, 3 kept, each changed by one atomic, so
 // readers see a whole state. Each round, an undecided candidate with no undecided higher-ranked
@@ -432,15 +443,21 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
 // up. Pushing the drops halves the rounds against drops found by the dropped candidates' owners
 // in the next round (8.1 -> 4.2 on the batched events).
 // The kept keys are then gathered into st (as many as its st_words hold) and ordered by rank (by
-// counting the kept keys above each, up to 1,024 of them; else bitonic). Returns
-// the count, or -1 (written nothing) past 64 rounds or st_words, or with more than 64
+// counting the kept keys above each, up to 1,024 of them; else bitonic). st_words: at least
+// ceil(NT NR / 16) rounded up to a multiple of 32. act: two lists of act_cap 16-bit entries.
+// Returns the count, or -1 (written nothing) past 64 rounds or st_words, or with more than 64
 // candidates a thread. s[2] .. s[5] used.
 template <class Cells>
 __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int maxp, const uint32_t* keys, int C,
                               uint32_t* st, int st_words, uint16_t* act, int act_cap, hough_peak* dst, int* s) {
   const int lane = threadIdx.x & 31, bd = blockDim.x;
   if (C > 64 * bd || C > 65536) return -1;
-  const int nst = (NT * NR + 15) >> 4;
+  // State word w lives at w ^ (w >> 5 & 31): the words of the same rows of neighbouring columns,
+  // which the lanes of a warp read together, then fall in different banks (unswizzled, a column
+  // of 256 rows is 16 words, and 32 columns would share 2 banks).
+  const int nst = ((((NT * NR + 15) >> 4) + 31) & ~31);
+  if (nst > st_words) return -1;
+  auto swz = [](int w) { return w ^ ((w >> 5) & 31); };
   for (int i = threadIdx.x; i < nst; i += bd) st[i] = 0u;
   if (threadIdx.x < 4) s[2 + threadIdx.x] = 0;
   __syncthreads();
@@ -461,12 +478,12 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       if (w == (b0 >> 5)) m &= 0xffffffffu << (b0 & 31);
       if (w == (b1 >> 5)) m &= 0xffffffffu >> (31 - (b1 & 31));
       if (w == (bc >> 5)) m &= ~(1u << (bc & 31));
-      atomicAnd(&st[w], ~m);
+      atomicAnd(&st[swz(w)], ~m);
     }
   };
-  for (int i = threadIdx.x; i < C; i += bd) {
+  for (int i = threadIdx.x; i < C; i += bd) {  // every candidate undecided
     const int c = cell_of(keys[i]);
-    atomicOr(&st[c >> 4], 1u << ((c & 15) << 1));
+    atomicOr(&st[swz(c >> 4)], 1u << ((c & 15) << 1));
   }
   __syncthreads();
   // The decision on undecided candidate (j, k) from the states of its window: 1 (drop) for a kept
@@ -486,8 +503,8 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
       for (int off = 0; off < nb && !drop && all; off += 32) {
         const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
-        uint32_t f = st[w] >> sh;
-        if (sh && sh + len > 32) f |= st[w + 1] << (32 - sh);
+        uint32_t f = st[swz(w)] >> sh;
+        if (sh && sh + len > 32) f |= st[swz(w + 1)] << (32 - sh);
         if (len < 32) f &= (1u << len) - 1u;
         if ((f & (f >> 1)) & 0x55555555u) {  // a kept cell
           drop = true;
@@ -512,11 +529,24 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       for (int a = lane - R; a <= R; a += 32) push_column(x >> 16, x & 0xffff, a);
     }
   };
+  // The drops of the kept ones among candidates L[0 .. n) (candidates 0 .. n without a list),
+  // pushed after the pass that kept them: a thread a (candidate, window column) pair. (Round 0's
+  // survivors: 14 k cycles an event against 17 k pushed in the pass by their warps; in the later
+  // rounds pushes in the pass are faster, since they drop candidates that the same round visits.)
+  auto push_kept = [&](const uint16_t* L, int n) {
+    const int W = 2 * R + 1;
+    for (int it = threadIdx.x; it < n * W; it += bd) {
+      const int e = it / W, a = it - e * W - R;
+      const uint32_t key = keys[L ? (int)L[e] : e];
+      const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u), c = j * NR + k;
+      if (((st[swz(c >> 4)] >> ((c & 15) << 1)) & 3u) == 3u) push_column(j, k, a);
+    }
+  };
   // Round 0 in three passes, since most candidates are not local maxima and a warp's scans last
   // as long as its slowest lane's. (1) A candidate with a higher-ranked cell among its eight
   // neighbours (votes alone decide: cells below the threshold rank below every candidate) stays
-  // undecided; the others are listed. (2) The listed ones are decided on their windows, a kept one
-  // pushing its drops. (3) The candidates still undecided are listed for round 1. Lists: act (the
+  // undecided; the others are listed. (2) The listed ones are decided on their windows, and the
+  // kept ones push their drops. (3) The candidates still undecided are listed for round 1. Lists: act (the
   // survivors), then act + act_cap (round 1's); s[4] counts the survivors, s[2] the undecided.
   {
     for (int t0 = threadIdx.x - lane; t0 < C; t0 += bd) {  // slots of a warp: uniform
@@ -538,10 +568,8 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
           sv = sv && kd <= key;
         }
       }
-      if (sv) {
-        const int pos = atomicAdd(&s[4], 1);
-        if (pos < act_cap) act[pos] = (uint16_t)t;
-      }
+      const int pos = warp_append(&s[4], sv);
+      if (sv && pos < act_cap) act[pos] = (uint16_t)t;
     }
     __syncthreads();
     const int ns = s[4], n = ns <= act_cap ? ns : C;  // past the list's room: every candidate
@@ -551,25 +579,20 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       const uint32_t key = keys[i];
       const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int c = j * NR + k;
-      int jk = -1;
-      if (t < n && ((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
+      if (t < n && ((st[swz(c >> 4)] >> ((c & 15) << 1)) & 3u) == 1u) {
         const int d = decide(j, k, key);
-        if (d == 1) {
-          atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
-        } else if (d == 2) {
-          atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
-          jk = (j << 16) | k;
-        }
+        if (d == 1) atomicAnd(&st[swz(c >> 4)], ~(1u << ((c & 15) << 1)));  // 1 -> 0
+        else if (d == 2) atomicOr(&st[swz(c >> 4)], 2u << ((c & 15) << 1));  // 1 -> 3
       }
-      push_slot(jk);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < C; i += bd) {
-      const int c = cell_of(keys[i]);
-      if (((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
-        const int pos = atomicAdd(&s[2], 1);
-        if (pos < act_cap) act[act_cap + pos] = (uint16_t)i;
-      }
+    push_kept(ns <= act_cap ? act : nullptr, n);
+    __syncthreads();
+    for (int i0 = threadIdx.x - lane; i0 < C; i0 += bd) {  // slots of a warp: uniform
+      const int i = i0 + lane, c = cell_of(keys[i < C ? i : 0]);
+      const bool u = i < C && ((st[swz(c >> 4)] >> ((c & 15) << 1)) & 3u) == 1u;
+      const int pos = warp_append(&s[2], u);
+      if (u && pos < act_cap) act[act_cap + pos] = (uint16_t)i;
     }
     __syncthreads();
   }
@@ -596,7 +619,7 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
         const uint32_t key = keys[i];
         const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
         const int c = j * NR + k;
-        const uint32_t sw = __shfl_sync(0xffffffffu, st[c >> 4], 0);  // one reading for the warp
+        const uint32_t sw = __shfl_sync(0xffffffffu, st[swz(c >> 4)], 0);  // one reading for the warp
         if (((sw >> ((c & 15) << 1)) & 3u) != 1u) continue;  // dropped since it was listed
         bool kept_seen = false, above = false;
         for (int q = lane; q < nc; q += 32) {
@@ -608,7 +631,7 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
             kk = NR - 1 - kk;
           }
           const int cc = jj * NR + kk;
-          const uint32_t sv = (st[cc >> 4] >> ((cc & 15) << 1)) & 3u;
+          const uint32_t sv = (st[swz(cc >> 4)] >> ((cc & 15) << 1)) & 3u;
           if (sv == 3u) {
             kept_seen = true;
           } else if (sv == 1u) {
@@ -620,9 +643,9 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
         kept_seen = __any_sync(0xffffffffu, kept_seen);
         above = __any_sync(0xffffffffu, above);
         if (kept_seen) {
-          if (lane == 0) atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
+          if (lane == 0) atomicAnd(&st[swz(c >> 4)], ~(1u << ((c & 15) << 1)));  // 1 -> 0
         } else if (!above) {
-          if (lane == 0) atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+          if (lane == 0) atomicOr(&st[swz(c >> 4)], 2u << ((c & 15) << 1));  // 1 -> 3
           if (lane < W) push_column(j, k, lane - R);
         } else if (lane == 0) {
           const int pos = atomicAdd(&s[2 + r3], 1);
@@ -636,19 +659,22 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       const uint32_t key = keys[i];
       const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int c = j * NR + k;
+      bool und = false;
       int jk = -1;
-      if (t < n_cur && ((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 1u) {
+      if (t < n_cur && ((st[swz(c >> 4)] >> ((c & 15) << 1)) & 3u) == 1u) {
         const int d = decide(j, k, key);
         if (d == 1) {
-          atomicAnd(&st[c >> 4], ~(1u << ((c & 15) << 1)));  // 1 -> 0
+          atomicAnd(&st[swz(c >> 4)], ~(1u << ((c & 15) << 1)));  // 1 -> 0
         } else if (d == 2) {
-          atomicOr(&st[c >> 4], 2u << ((c & 15) << 1));  // 1 -> 3
+          atomicOr(&st[swz(c >> 4)], 2u << ((c & 15) << 1));  // 1 -> 3
           jk = (j << 16) | k;
-        } else {  // counted, and listed for the next round while the list has room
-          const int pos = atomicAdd(&s[2 + r3], 1);
-          if (pos < act_cap) nxt[pos] = (uint16_t)i;
+        } else {
+          und = true;
         }
       }
+      // the undecided are counted, and listed for the next round while the list has room
+      const int pos = warp_append(&s[2 + r3], und);
+      if (und && pos < act_cap) nxt[pos] = (uint16_t)i;
       push_slot(jk);
     }
     // undecided count: three rotating counters, so that one barrier a round suffices
@@ -665,7 +691,7 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     int t = 0;
     for (int i = threadIdx.x; i < C; i += bd, ++t) {
       const int c = cell_of(keys[i]);
-      if (((st[c >> 4] >> ((c & 15) << 1)) & 3u) == 3u) flags |= 1ull << t;
+      if (((st[swz(c >> 4)] >> ((c & 15) << 1)) & 3u) == 3u) flags |= 1ull << t;
     }
   }
   {
@@ -681,8 +707,11 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
   __syncthreads();
   {
     int t = 0;
-    for (int i = threadIdx.x; i < C; i += bd, ++t) {
-      if ((flags >> t) & 1ull) st[atomicAdd(&s[4], 1)] = keys[i];
+    for (int i0 = threadIdx.x - lane; i0 < C; i0 += bd, ++t) {  // slots of a warp: uniform
+      const int i = i0 + lane;
+      const bool kp = i < C && ((flags >> t) & 1ull);
+      const int pos = warp_append(&s[4], kp);
+      if (kp) st[pos] = keys[i];
     }
   }
   __syncthreads();
@@ -775,7 +804,7 @@ __device__ inline int resolve_walk(int NT, int NR, int R, int maxp, uint32_t* ke
 // st_words > 0, else (or when the rounds give up) by the walk; otherwise one pass per peak.
 // scratch (shared): max(iter_scratch_words(NT, NR, SH), cap + max(ceil(NT NR / 32), st_words))
 // words when sup is null: the candidate keys, then the walk's bitmap, or the rounds' states
-// (st_words >= ceil(NT NR / 16), a power of two). With sup given (a shared bitmap of NT NR
+// (st_words >= ceil(NT NR / 16) rounded up to 32 words). With sup given (a shared bitmap of NT NR
 // bits, left set) the walk uses it, and scratch needs max(iter_scratch_words, cap + st_words).
 template <class Cells>
 __device__ int extract_iterative(Cells& cells, int NT, int NR, int SH, int thr, int rel_num, int rel_den, int R,

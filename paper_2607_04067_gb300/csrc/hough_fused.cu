@@ -1738,7 +1738,7 @@ __device__ void run_item(const Plan& pl, const FusedIO& io, unsigned char* smem,
       __syncthreads();
       HOUGH_PHASE(HOUGH_PHASE_SCAN);
       HOUGH_PHASE(HOUGH_PHASE_SCAN);
-      const int st_words = (NT * NR + 15) >> 4;
+      const int st_words = (((NT * NR + 15) >> 4) + 31) & ~31;  // 2 bits a cell, whole 32-word blocks
       return extract_iterative(cells, NT, NR, kIterSliceRows, pl.threshold, pl.rel_num, pl.rel_den, pl.nms_radius,
                                maxp, pbits, pl.iter_cap, nullptr, st_words, io.peaks + e * (long long)maxp, sh.tmp,
                                reinterpret_cast<uint16_t*>(pbits + pl.iter_cap + st_words), pl.iter_act);
