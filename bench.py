@@ -171,6 +171,14 @@ def oracle_baseline(cfg, ev, budget_events: int, threads: int, peak=(0, 0, 1, 1)
     return n / dt, r, n, dt
 
 
+def sized_sample(cfg, ev, want: int, threads: int, peak, seconds: float) -> int:
+    """Events of a CPU sample of about `seconds` (at most `want`), sized from a short probe run, so
+    that slow oracle configurations (the iterative finder at 512 x 512) stay within a bounded time."""
+    probe = min(want, max(32, 8 * threads))
+    v, _, _, _ = oracle_baseline(cfg, ev, probe, threads, peak)
+    return max(probe, min(want, int(v * seconds)))
+
+
 def run_reference(args, cfg):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -516,7 +524,7 @@ def main():
     ap.add_argument("--events", type=int, default=0, help="events per rank (0 = the workload's size)")
     ap.add_argument("--ref-events", type=int, default=3000, help="oracle events per reference step")
     ap.add_argument("--cpu-sample", type=int, default=10000,
-                    help="oracle events for cpu_baseline (a tenth of them for the single-thread run)")
+                    help="most oracle events for cpu_baseline and parity (sized to ~20 s; ~15 s on one thread)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each serving stream")
@@ -690,13 +698,16 @@ def main():
     hbm_bytes = ev.n_hits * 9 + n_events * 16 + stored * PEAK_RECORD_BYTES
     clk = clocks.summary()
 
-    # parity of the timed batch itself: its first --cpu-sample events against the oracle
+    # parity of the timed batch itself: its first events (up to --cpu-sample, about 20 s of the
+    # oracle on the host threads) against the oracle
     cpu = parity = None
     if not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, r, n, dt = oracle_baseline(cfg, ev, args.cpu_sample, threads, peak_args(args))
+        n_par = sized_sample(cfg, ev, args.cpu_sample, threads, peak_args(args), 20.0)
+        v, r, n, dt = oracle_baseline(cfg, ev, n_par, threads, peak_args(args))
         parity = compare_with_oracle(r, n, ev, out, cfg.max_peaks)
-        v1, _, n1, dt1 = oracle_baseline(cfg, ev, max(1, args.cpu_sample // 10), 1, peak_args(args))
+        n_one = max(1, min(n // 10, int(v / threads * 15.0)))  # about 15 s on one thread
+        v1, _, n1, dt1 = oracle_baseline(cfg, ev, n_one, 1, peak_args(args))
         cpu = {"value": v, "unit": "events/s", "cores": threads, "kind": "oracle",
                "sample": f"first {n} events of this batch ({dt:.1f} s wall on {threads} threads, events in parallel)",
                "single_thread": {"value": v1, "unit": "events/s", "cores": 1,

@@ -10,10 +10,18 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "hough.h"
 
 namespace hgpu {
+
+// Cells given as a sorted candidate list (kSorted: lower(j, k), end(j), key(p), rows ascending in
+// a column) let the rounds walk a column instead of looking every cell up.
+template <class C, class = void>
+struct sorted_cells : std::false_type {};
+template <class C>
+struct sorted_cells<C, std::void_t<decltype(C::kSorted)>> : std::bool_constant<C::kSorted> {};
 
 // Phase timers (builds with HOUGH_PHASE_TIMERS defined): thread 0 of a CTA adds the clock64()
 // cycles since its previous mark to the counter of the phase that just ended (HOUGH_PHASE_*).
@@ -501,6 +509,11 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       }
       // the states of rows r0 .. r1 of column jj, 16 cells at a time
       const int b0 = (jj * NR + r0) << 1, nb = (r1 - r0 + 1) << 1;
+      int p = 0, e_col = 0;  // sorted lists: a walk down column jj's list
+      if constexpr (sorted_cells<Cells>::value) {
+        p = cells.lower(jj, r0);
+        e_col = cells.end(jj);
+      }
       for (int off = 0; off < nb && !drop && all; off += 32) {
         const int bb = b0 + off, w = bb >> 5, sh = bb & 31, len = min(32, nb - off);
         uint32_t f = st[swz(w)] >> sh;
@@ -513,8 +526,13 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
         uint32_t m = f & ~(f >> 1) & 0x55555555u;  // undecided cells
         while (m && all) {
           const int kr = r0 + ((off + __ffs(m) - 1) >> 1);
-          const uint32_t kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) |
-                              (uint32_t)(1023 - kr);
+          uint32_t kd;
+          if constexpr (sorted_cells<Cells>::value) {  // an undecided cell is in its column's list
+            while (p < e_col && 1023 - (int)(cells.key(p) & 1023u) < kr) ++p;
+            kd = p < e_col ? cells.key(p) : 0u;
+          } else {
+            kd = ((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) | (uint32_t)(1023 - kr);
+          }
           if (kd > key) all = false;  // an undecided cell ranked above (the cell itself is equal)
           m &= m - 1u;
         }
@@ -552,7 +570,24 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
     for (int t0 = threadIdx.x - lane; t0 < C; t0 += bd) {  // slots of a warp: uniform
       const int t = t0 + lane;
       bool sv = t < C;
-      if (sv && R > 0) {
+      if (sv && R > 0 && sorted_cells<Cells>::value) {  // three column walks
+        const uint32_t key = keys[t];
+        const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
+        for (int da = -1; da <= 1; ++da) {
+          int jj = j + da, r0 = max(0, k - 1), r1 = min(NR - 1, k + 1);
+          if (jj < 0 || jj >= NT) {  // across the theta wrap: the other end, rho mirrored
+            jj = jj < 0 ? jj + NT : jj - NT;
+            const int t0 = NR - 1 - r1;
+            r1 = NR - 1 - r0;
+            r0 = t0;
+          }
+          if constexpr (sorted_cells<Cells>::value) {
+            const int e_col = cells.end(jj);
+            for (int p = cells.lower(jj, r0); p < e_col && 1023 - (int)(cells.key(p) & 1023u) <= r1; ++p)
+              sv = sv && cells.key(p) <= key;
+          }
+        }
+      } else if (sv && R > 0) {
         const uint32_t key = keys[t];
         const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
 #pragma unroll

@@ -1273,18 +1273,24 @@ struct SparseCands {
 // the row within its column's list by binary search.
 struct ListCells {
   static constexpr bool kPairs = false;
+  static constexpr bool kSorted = true;  // the rounds walk a column's list instead of searching each cell
   const uint32_t* keys;
   const int* colstart;
-  __device__ int get(int j, int k) const {
-    int lo = colstart[j];
-    const int end = colstart[j + 1];
-    int hi = end;
+  // first candidate of column j at row k or below it in the list (rows ascend), else the column's end
+  __device__ int lower(int j, int k) const {
+    int lo = colstart[j], hi = colstart[j + 1];
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if (1023 - (int)(keys[mid] & 1023u) < k) lo = mid + 1;
       else hi = mid;
     }
-    return (lo < end && 1023 - (int)(keys[lo] & 1023u) == k) ? (int)(keys[lo] >> 20) : 0;
+    return lo;
+  }
+  __device__ int end(int j) const { return colstart[j + 1]; }
+  __device__ uint32_t key(int p) const { return keys[p]; }
+  __device__ int get(int j, int k) const {
+    const int lo = lower(j, k);
+    return (lo < colstart[j + 1] && 1023 - (int)(keys[lo] & 1023u) == k) ? (int)(keys[lo] >> 20) : 0;
   }
 };
 
