@@ -563,8 +563,8 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
   // Round 0 in three passes, since most candidates are not local maxima and a warp's scans last
   // as long as its slowest lane's. (1) A candidate with a higher-ranked cell among its eight
   // neighbours (votes alone decide: cells below the threshold rank below every candidate) stays
-  // undecided; the others are listed. (2) The listed ones are decided on their windows, and the
-  // kept ones push their drops. (3) The candidates still undecided are listed for round 1. Lists: act (the
+  // undecided; the others are listed. (2) The listed ones that rank above their whole window are
+  // kept, and push their drops. (3) The candidates still undecided are listed for round 1. Lists: act (the
   // survivors), then act + act_cap (round 1's); s[4] counts the survivors, s[2] the undecided.
   {
     for (int t0 = threadIdx.x - lane; t0 < C; t0 += bd) {  // slots of a warp: uniform
@@ -614,10 +614,30 @@ __device__ int resolve_rounds(Cells& cells, int NT, int NR, int R, int tq, int m
       const uint32_t key = keys[i];
       const int j = 1023 - (int)((key >> 10) & 1023u), k = 1023 - (int)(key & 1023u);
       const int c = j * NR + k;
-      if (t < n && ((st[swz(c >> 4)] >> ((c & 15) << 1)) & 3u) == 1u) {
-        const int d = decide(j, k, key);
-        if (d == 1) atomicAnd(&st[swz(c >> 4)], ~(1u << ((c & 15) << 1)));  // 1 -> 0
-        else if (d == 2) atomicOr(&st[swz(c >> 4)], 2u << ((c & 15) << 1));  // 1 -> 3
+      // at the start of round 0 every candidate is undecided and none is kept, so the rules keep
+      // exactly the candidates that rank above every other cell of their window: a test on the
+      // votes alone, with independent reads (the state scan's reads depend on one another)
+      if (t < n) {
+        bool top = true;
+        const int k0 = max(0, k - R), k1 = min(NR - 1, k + R);
+        for (int a = -R; a <= R; ++a) {
+          int jj = j + a, r0 = k0, r1 = k1;
+          if (jj < 0 || jj >= NT) {  // across the theta wrap: the other end, rho mirrored
+            jj = jj < 0 ? jj + NT : jj - NT;
+            r0 = NR - 1 - k1;
+            r1 = NR - 1 - k0;
+          }
+          if constexpr (sorted_cells<Cells>::value) {
+            const int e_col = cells.end(jj);
+            for (int p = cells.lower(jj, r0); p < e_col && 1023 - (int)(cells.key(p) & 1023u) <= r1; ++p)
+              top &= cells.key(p) <= key;
+          } else {
+#pragma unroll 4
+            for (int kr = r0; kr <= r1; ++kr)
+              top &= (((uint32_t)cells.get(jj, kr) << 20) | ((uint32_t)(1023 - jj) << 10) | (uint32_t)(1023 - kr)) <= key;
+          }
+        }
+        if (top) atomicOr(&st[swz(c >> 4)], 2u << ((c & 15) << 1));  // 1 -> 3
       }
     }
     __syncthreads();

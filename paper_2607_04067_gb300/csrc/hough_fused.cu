@@ -1272,7 +1272,6 @@ struct SparseCands {
 // Votes of a cell that is a candidate of a sparse list (the dense rounds only ask for candidates):
 // the row within its column's list by binary search.
 struct ListCells {
-  static constexpr bool kPairs = false;
   static constexpr bool kSorted = true;  // the rounds walk a column's list instead of searching each cell
   const uint32_t* keys;
   const int* colstart;
