@@ -543,7 +543,7 @@ def test_iterative_matches_greedy_restatement(seed):
     assert [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk] == exp
 
 
-def _rounds_peaks(acc, T, num, den, R, push=False, order_rng=None):
+def _rounds_peaks(acc, T, num, den, R, push=False, order_rng=None, window_max_round0=False):
     """The kept set reached by rounds of local rules (no ordering of the work): a candidate
     (cell passing the thresholds) is dropped once a kept candidate lies in its window, and kept
     once every higher-ranked candidate in its window is dropped; rank is (votes desc, raster
@@ -551,13 +551,25 @@ def _rounds_peaks(acc, T, num, den, R, push=False, order_rng=None):
     before. With push, a candidate kept in a round also drops every undecided candidate of its
     window at once. With order_rng, a round visits the candidates in a random order and each
     decision (and push) is seen by the visits after it (the GPU's threads read states while
-    others change them). The kept cells, listed in rank order."""
+    others change them). With window_max_round0, round 0 keeps exactly the candidates whose
+    window holds no cell of more votes (ties by raster order), read from the votes alone, and
+    pushes their drops: the GPU's round 0. The kept cells, listed in rank order."""
     NT, NR = acc.shape
     amax = int(acc.max()) if acc.size else 0
     cand = [(j, k) for j in range(NT) for k in range(NR) if acc[j, k] >= T and int(acc[j, k]) * den >= num * amax]
     rank = {c: (-int(acc[c]), c[0] * NR + c[1]) for c in cand}
     window = {c: [d for d in cand if d != c and _in_window(c, d, R, NT, NR)] for c in cand}
     state = {c: 0 for c in cand}  # 0 undecided, 1 dropped, 2 kept
+    if window_max_round0:
+        cells = [(j, k) for j in range(NT) for k in range(NR)]
+        rank_all = {c: (-int(acc[c]), c[0] * NR + c[1]) for c in cells}
+        top = [c for c in cand if all(rank_all[d] > rank_all[c] for d in cells if d != c and _in_window(c, d, R, NT, NR))]
+        for c in top:
+            state[c] = 2
+        for c in top:
+            for d in window[c]:
+                assert state[d] != 2
+                state[d] = 1
     for _ in range(len(cand) + 1):
         new = dict(state)
         seen = new if order_rng is not None else state  # in place: later visits see earlier ones
@@ -601,9 +613,9 @@ def test_iterative_local_rules_reach_the_greedy_list(seed):
     n, pk = oracle.peaks_iterative(acc, p)
     exp = [((int(q["theta_bin"]), int(q["rho_bin"])), int(q["votes"])) for q in pk]
     # synchronous rounds, with and without pushed drops, and in-place rounds in random orders
-    for push, order in ((False, None), (True, None), (True, np.random.default_rng(seed)),
-                        (False, np.random.default_rng(50 + seed))):
-        got = _rounds_peaks(acc, T, num, den, R, push=push, order_rng=order)
+    for push, order, w0 in ((False, None, False), (True, None, False), (True, np.random.default_rng(seed), False),
+                            (False, np.random.default_rng(50 + seed), False), (True, np.random.default_rng(seed), True)):
+        got = _rounds_peaks(acc, T, num, den, R, push=push, order_rng=order, window_max_round0=w0)
         assert n == len(got)
         assert exp == got, (push, order is not None)
 
