@@ -363,12 +363,15 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
   // consecutive words of two columns each: w and NT - 1 - w)
   {
     int m = 0;
-    if constexpr (Cells::kPairs) {
-      for (int k = warp; k < NR; k += nwarps)
-        for (int w = lane; w < cells.words(); w += 32) {
-          const uint32_t x = cells.word(w, k);
-          m = max(m, (int)max(x & 0xffffu, x >> 16));
-        }
+    if constexpr (Cells::kPairs) {  // four words a lane, both halves at once (16-bit SIMD maxima)
+      const int W4 = (cells.words() + 3) >> 2, n4 = NR * W4;
+      unsigned mm = 0u;
+      for (int it = threadIdx.x; it < n4; it += blockDim.x) {
+        const int k = it / W4;
+        const uint4 x = cells.words4((it - k * W4) << 2, k);
+        mm = __vmaxu2(mm, __vmaxu2(__vmaxu2(x.x, x.y), __vmaxu2(x.z, x.w)));
+      }
+      m = (int)max(mm & 0xffffu, mm >> 16);
     } else {
       for (int k = warp; k < NR; k += nwarps)
         for (int j = lane; j < NT; j += 32) m = max(m, cells.get(j, k));
@@ -387,22 +390,47 @@ __device__ int collect_candidates(Cells& cells, int NT, int NR, int thr, int rel
     return ((uint32_t)v << 20) | ((uint32_t)(1023 - j) << 10) | (uint32_t)(1023 - k);
   };
   if constexpr (Cells::kPairs) {
-    const int Wd = cells.words();
-    for (int k = warp; k < NR; k += nwarps) {
-      for (int w0 = 0; w0 < Wd; w0 += 32) {
-        const int w = w0 + lane;
-        const uint32_t x = w < Wd ? cells.word(w, k) : 0u;
-        const int vl = (int)(x & 0xffffu), vh = (int)(x >> 16);
-        const bool cl = w < Wd && vl >= tq, ch = w < Wd && vh >= tq;
-        const uint32_t bl = __ballot_sync(0xffffffffu, cl), bh = __ballot_sync(0xffffffffu, ch);
-        if (bl | bh) {
-          int base = 0;
-          if (lane == 0) base = atomicAdd(&s[1], __popc(bl) + __popc(bh));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          const uint32_t lt = (1u << lane) - 1u;
-          const int pl = base + __popc(bl & lt), ph = base + __popc(bl) + __popc(bh & lt);
-          if (cl && pl < cap) keys[pl] = key_of(vl, w, k);
-          if (ch && ph < cap) keys[ph] = key_of(vh, cells.mirror_col(w), k);
+    // four words (eight cells) a lane; a warp's candidates get consecutive positions (one
+    // atomic a warp), each lane's in word order, low half first. (Two passes without atomics,
+    // a warp counting its run of rows before writing, measured slower: 22.1 k against 12.7 k.)
+    const int Wd = cells.words(), W4 = (Wd + 3) >> 2, n4 = NR * W4;
+    const unsigned tq2 = (unsigned)tq * 0x10001u;
+    for (int it0 = threadIdx.x - lane; it0 < n4; it0 += blockDim.x) {  // slots of a warp: uniform
+      const int it = it0 + lane, k = it / W4, w4 = (it - k * W4) << 2;
+      unsigned ge[4] = {0u, 0u, 0u, 0u};
+      uint4 x = make_uint4(0u, 0u, 0u, 0u);
+      if (it < n4) {
+        x = cells.words4(w4, k);
+        ge[0] = __vcmpgeu2(x.x, tq2);
+        ge[1] = w4 + 1 < Wd ? __vcmpgeu2(x.y, tq2) : 0u;  // words past the tile's own: none
+        ge[2] = w4 + 2 < Wd ? __vcmpgeu2(x.z, tq2) : 0u;
+        ge[3] = w4 + 3 < Wd ? __vcmpgeu2(x.w, tq2) : 0u;
+      }
+      int n = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) n += (ge[q] & 1u) + (ge[q] >> 31);
+      int pre = n;  // inclusive scan over the warp's lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, pre, 31);
+      int base = 0;
+      if (lane == 31 && total) base = atomicAdd(&s[1], total);
+      base = __shfl_sync(0xffffffffu, base, 31) + pre - n;
+      if (n) {
+        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (ge[q] & 1u) {
+            if (base < cap) keys[base] = key_of((int)(xs[q] & 0xffffu), w4 + q, k);
+            ++base;
+          }
+          if (ge[q] >> 31) {
+            if (base < cap) keys[base] = key_of((int)(xs[q] >> 16), cells.mirror_col(w4 + q), k);
+            ++base;
+          }
         }
       }
     }

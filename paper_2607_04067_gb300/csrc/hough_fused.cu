@@ -402,6 +402,11 @@ struct FusedCells {
   __device__ int words() const { return Wd; }
   __device__ int mirror_col(int w) const { return 2 * Wd - 1 - w; }
   __device__ uint32_t word(int w, int k) const { return acc[mp_word(w, k + 1, rp)]; }
+  // words w4 .. w4 + 3 of row k (w4 a multiple of 4: all four in one 32-word group, 16-byte aligned;
+  // words past the tile's own are zero)
+  __device__ uint4 words4(int w4, int k) const {
+    return *reinterpret_cast<const uint4*>(acc + mp_word(w4, k + 1, rp));
+  }
   __device__ int get(int j, int k) const {
     if (MP) {
       const bool hi = j >= Wd;
